@@ -1,0 +1,227 @@
+"""FP64 CPU oracle for the asqtad even-odd CG -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` import this package.  The GPU library neither imports nor links
+it, and the two share no code: the oracle is plain C (``oracle.c``) written
+site by site from the operator definitions, driven through ctypes.
+
+Vectors here are numpy complex128 arrays.  Full-lattice vectors have shape
+``(V, 3)`` indexed by ``site_lex``; parity-half vectors have shape
+``(V/2, 3)`` indexed by ``i = site_lex // 2`` within the parity.
+``embed_half``/``extract_half`` convert between the two.
+
+Parity: every function is pinned by the CPU tests (``tests/test_oracle_*``)
+against closed forms, invariants and dense linear algebra; see the header of
+``oracle.c`` for the definitions it follows.
+"""
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, 'oracle.c')
+_LIB = os.path.join(_HERE, 'liboracle.so')
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ['-O2', '-std=c11', '-fopenmp', '-ffp-contract=off', '-fPIC', '-shared']
+
+
+def build(force=False):
+    """Compile oracle.c into liboracle.so next to it (gcc, OpenMP)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + '.%d.tmp' % os.getpid()
+    subprocess.check_call(['gcc'] + CFLAGS + ['-o', tmp, _SRC, '-lm'])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            I = ctypes.c_int
+            Lg = ctypes.c_long
+            D = ctypes.c_double
+            lib.oracle_dslash.argtypes = [P, P, P, I, I, P, P]
+            lib.oracle_dslash_site.argtypes = [P, P, P, I, Lg, P, P]
+            lib.oracle_mdagm.argtypes = [P, P, P, I, D, P, P, P]
+            lib.oracle_true_residual.argtypes = [P, P, P, I, D, P, P]
+            lib.oracle_true_residual.restype = D
+            lib.oracle_cg.argtypes = [P, P, P, I, D, P, D, I, P, P]
+            lib.oracle_cg.restype = I
+            lib.oracle_cg_multishift.argtypes = [P, P, P, I, I, P, P, D, I, P, P]
+            lib.oracle_cg_multishift.restype = I
+            lib.oracle_neighbor.argtypes = [P, Lg, I, I, I, P]
+            lib.oracle_neighbor.restype = Lg
+            lib.oracle_eta.argtypes = [P, Lg, I]
+            lib.oracle_eta.restype = I
+            lib.oracle_parity.argtypes = [P, Lg]
+            lib.oracle_parity.restype = I
+            lib.oracle_quantize_spinor_i16.argtypes = [Lg, P, P, P]
+            lib.oracle_quantize_links_i16.argtypes = [Lg, P, D, P]
+            _lib = lib
+    return _lib
+
+
+def _dims(dims):
+    return np.ascontiguousarray(np.asarray(dims, dtype=np.int32))
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def volume(dims):
+    return int(np.prod(np.asarray(dims, dtype=np.int64)))
+
+
+def half_sites(dims, parity):
+    """site_lex of the parity's sites in half-lattice order."""
+    lx, ly, lz, lt = (int(d) for d in dims)
+    lex = np.arange(volume(dims))
+    x = lex % lx
+    y = (lex // lx) % ly
+    z = (lex // (lx * ly)) % lz
+    t = lex // (lx * ly * lz)
+    return lex[((x + y + z + t) & 1) == parity]
+
+
+def embed_half(dims, parity, v):
+    full = np.zeros((volume(dims), 3), dtype=np.complex128)
+    full[half_sites(dims, parity)] = v
+    return full
+
+
+def extract_half(dims, parity, full):
+    return np.ascontiguousarray(full[half_sites(dims, parity)])
+
+
+# ----------------------------------------------------------------- lattice
+
+def neighbor(dims, s, mu, d, t_sign=1):
+    """(site_lex of x + d*mu_hat, boundary sign)."""
+    lib = _load()
+    sg = ctypes.c_int(0)
+    n = lib.oracle_neighbor(_ptr(_dims(dims)), int(s), int(mu), int(d), int(t_sign),
+                            ctypes.byref(sg))
+    return n, sg.value
+
+
+def eta(dims, s, mu):
+    return _load().oracle_eta(_ptr(_dims(dims)), int(s), int(mu))
+
+
+def parity(dims, s):
+    return _load().oracle_parity(_ptr(_dims(dims)), int(s))
+
+
+# ----------------------------------------------------------------- operators
+
+def dslash(dims, fat, lng, v, out_parity=-1, t_sign=1):
+    """Full-lattice D applied to v (V, 3); rows of parity out_parity (or all)."""
+    lib = _load()
+    fat, lng, v = _c128(fat), _c128(lng), _c128(v)
+    out = np.zeros((volume(dims), 3), dtype=np.complex128)
+    lib.oracle_dslash(_ptr(_dims(dims)), _ptr(fat), _ptr(lng), int(t_sign), int(out_parity),
+                      _ptr(v), _ptr(out))
+    return out
+
+
+def dslash_half(dims, fat, lng, v_half, out_parity, t_sign=1):
+    """D_{p,1-p}: parity-half input of parity 1-p to parity-half output p."""
+    full = embed_half(dims, 1 - out_parity, v_half)
+    return extract_half(dims, out_parity, dslash(dims, fat, lng, full, out_parity, t_sign))
+
+
+def dslash_site(dims, fat, lng, v, site_lex, t_sign=1):
+    """One output site (3,) of D applied to the full-lattice vector v."""
+    lib = _load()
+    fat, lng, v = _c128(fat), _c128(lng), _c128(v)
+    out = np.zeros(3, dtype=np.complex128)
+    lib.oracle_dslash_site(_ptr(_dims(dims)), _ptr(fat), _ptr(lng), int(t_sign), int(site_lex),
+                           _ptr(v), _ptr(out))
+    return out
+
+
+def mdagm(dims, fat, lng, mass, p_even, t_sign=1):
+    """A p = m^2 p - D_eo D_oe p on the even half (input and output (V/2, 3))."""
+    lib = _load()
+    fat, lng = _c128(fat), _c128(lng)
+    p = embed_half(dims, 0, p_even)
+    out = np.zeros_like(p)
+    tmp = np.zeros_like(p)
+    lib.oracle_mdagm(_ptr(_dims(dims)), _ptr(fat), _ptr(lng), int(t_sign), float(mass),
+                     _ptr(p), _ptr(out), _ptr(tmp))
+    return extract_half(dims, 0, out)
+
+
+def true_residual(dims, fat, lng, mass, b_even, x_even, t_sign=1):
+    """|b - A x| / |b| in FP64 (even half vectors)."""
+    lib = _load()
+    fat, lng = _c128(fat), _c128(lng)
+    b = embed_half(dims, 0, b_even)
+    x = embed_half(dims, 0, x_even)
+    return lib.oracle_true_residual(_ptr(_dims(dims)), _ptr(fat), _ptr(lng), int(t_sign),
+                                    float(mass), _ptr(b), _ptr(x))
+
+
+def cg(dims, fat, lng, mass, b_even, tol, max_iter=100000, t_sign=1):
+    """FP64 CG on A x = b.  Returns (x_even, iterations or -1, true residual)."""
+    lib = _load()
+    fat, lng = _c128(fat), _c128(lng)
+    b = embed_half(dims, 0, b_even)
+    x = np.zeros_like(b)
+    tr = ctypes.c_double(0)
+    it = lib.oracle_cg(_ptr(_dims(dims)), _ptr(fat), _ptr(lng), int(t_sign), float(mass),
+                       _ptr(b), float(tol), int(max_iter), _ptr(x), ctypes.byref(tr))
+    return extract_half(dims, 0, x), it, tr.value
+
+
+def cg_multishift(dims, fat, lng, masses, b_even, tol, max_iter=100000, t_sign=1):
+    """Multi-shift CG.  Returns (x (nshift, V/2, 3), iterations, true residuals)."""
+    lib = _load()
+    fat, lng = _c128(fat), _c128(lng)
+    masses = np.ascontiguousarray(masses, dtype=np.float64)
+    ns = len(masses)
+    b = embed_half(dims, 0, b_even)
+    x = np.zeros((ns,) + b.shape, dtype=np.complex128)
+    tr = np.zeros(ns)
+    it = lib.oracle_cg_multishift(_ptr(_dims(dims)), _ptr(fat), _ptr(lng), int(t_sign), ns,
+                                  _ptr(masses), _ptr(b), float(tol), int(max_iter), _ptr(x),
+                                  _ptr(tr))
+    return np.stack([extract_half(dims, 0, x[i]) for i in range(ns)]), it, tr
+
+
+# ----------------------------------------------------------------- int16 codes
+
+def quantize_spinor_i16(v_half):
+    """int16 codes (n, 6) and FP32 site norms (n,) of an (n, 3) complex field."""
+    lib = _load()
+    v = _c128(v_half)
+    n = v.shape[0]
+    q = np.zeros((n, 6), dtype=np.int16)
+    norm = np.zeros(n, dtype=np.float32)
+    lib.oracle_quantize_spinor_i16(n, _ptr(v), _ptr(q), _ptr(norm))
+    return q, norm
+
+
+def quantize_links_i16(values, scale):
+    """int16 codes of real link elements with one global scale."""
+    lib = _load()
+    v = np.ascontiguousarray(values, dtype=np.float64).ravel()
+    q = np.zeros(v.shape[0], dtype=np.int16)
+    lib.oracle_quantize_links_i16(v.shape[0], _ptr(v), float(scale), _ptr(q))
+    return q.reshape(np.shape(values))
