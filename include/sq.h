@@ -1,0 +1,234 @@
+/*
+ * sq.h -- C ABI of the GB300-native asqtad staggered CG library.
+ *
+ * The library solves (m^2 - D_eo D_oe) x = b on the even sites of a 4-d
+ * lattice, where D is the asqtad (improved staggered) Dirac operator with
+ * fat one-hop links F and long three-hop (Naik) links L:
+ *
+ *   (D psi)(x) = 1/2 sum_mu eta_mu(x) [ F_mu(x) psi(x+mu) - F_mu(x-mu)^dag psi(x-mu)
+ *                                      + L_mu(x) psi(x+3mu) - L_mu(x-3mu)^dag psi(x-3mu) ]
+ *
+ * with eta_0 = 1, eta_1 = (-1)^x, eta_2 = (-1)^(x+y), eta_3 = (-1)^(x+y+z).
+ * This is the mixed-precision CG inverter for asqtad quarks that the paper
+ * ("Code Optimization on Kepler GPUs and Xeon Phi", Sec. 2, Fig. 1 and
+ * Table 2; Sec. 3, Table 4) times on a 20^3 x 64 lattice, and the entry
+ * points play the part of the application-to-solver interface of Sec. 3
+ * (the staggered-CG call the authors added between CPS and QUDA).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * dims      int[4] = {Lx, Ly, Lz, Lt}; every extent even and >= 2; V = product,
+ *           Vh = V/2.
+ * site_lex  x + Lx*(y + Ly*(z + Lz*t)).
+ * links     host/device array [site_lex][mu][row][col] of complex128
+ *           (interleaved re, im), mu = 0..3 for x, y, z, t; 4*9*V complex.
+ *           Fat links carry c1 and long links carry c3 (no coefficient is
+ *           applied inside the library).
+ * vectors   parity-half colour vectors in "canonical" layout: [i][colour]
+ *           complex128, i = site_lex / 2 ranking the parity's sites; 3*Vh
+ *           complex.  Solves act on the even parity.
+ * packed    the library's device layout for one parity-half vector, used by
+ *           dslash_apply and mdagm_apply (see sq_spinor_bytes):
+ *             SQ_PREC_F64: 3 planes of double2 (colour c at plane c);
+ *             SQ_PREC_F32: a float4 plane (c0.re, c0.im, c1.re, c1.im) then a
+ *                          float2 plane (c2.re, c2.im);
+ *             SQ_PREC_I16: one 16-byte record per site: three 32-bit words
+ *                          holding the colour's (re, im) 16-bit codes (re in
+ *                          the low half) as excess-32768 integers, then the
+ *                          site norm n as an FP32; value = code * n / 32767.
+ *           A plane holds `stride` sites (Vh rounded up to a multiple of 64).
+ * streams   `void *stream` is a cudaStream_t (NULL: the context's stream).
+ * errors    every call returns an sq_status; nothing aborts or throws.
+ *           Non-finite inputs give SQ_ERR_NONFINITE.
+ * ownership the caller owns every pointer it passes; calls that take host
+ *           data copy it before returning.  The library owns the device
+ *           memory behind contexts and gauge ids.
+ */
+#ifndef SQ_H
+#define SQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sq_ctx sq_ctx;
+
+typedef enum {
+    SQ_OK = 0,
+    SQ_PENDING = 1,          /* serve_poll: not finished within the timeout     */
+    SQ_NOT_CONVERGED = 2,    /* max_iter reached; x and stats are still written */
+    SQ_ERR_ARG = -1,
+    SQ_ERR_OOM = -2,         /* device allocation or the HBM budget refused     */
+    SQ_ERR_CUDA = -3,
+    SQ_ERR_NONFINITE = -4,
+    SQ_ERR_TIMEOUT = -5,
+    SQ_ERR_BUSY = -6,
+    SQ_ERR_NOTFOUND = -7,
+    SQ_ERR_UNSUPPORTED = -8  /* e.g. 12-real long links on links that are not c*SU(3) */
+} sq_status;
+
+typedef enum { SQ_PREC_F64 = 0, SQ_PREC_F32 = 1, SQ_PREC_I16 = 2 } sq_prec;
+
+/* gauge_load flags */
+#define SQ_GAUGE_DEVICE_PTRS    0x1u  /* fat/lng are device pointers              */
+#define SQ_GAUGE_ANTIPERIODIC_T 0x2u  /* hops that wrap around t pick up -1        */
+#define SQ_GAUGE_NO_F32         0x10u /* skip the FP32 forms                      */
+#define SQ_GAUGE_NO_I16         0x20u /* skip the 16-bit forms                    */
+#define SQ_GAUGE_NO_LONG12      0x40u /* skip the 12-real long-link forms         */
+
+/* sq_cg_opts.flags */
+#define SQ_CG_DEVICE_PTRS   0x1u  /* src/x are device pointers (canonical layout) */
+#define SQ_CG_INITIAL_GUESS 0x2u  /* x holds the starting guess on input          */
+#define SQ_CG_NO_GRAPH      0x4u  /* launch kernels directly, no CUDA graph       */
+
+typedef struct {
+    int precision;     /* sloppy precision: SQ_PREC_F64 = plain FP64 CG (default F32) */
+    int long_recon;    /* 18 or 12: long links stored 18-real or 12-real (default 18) */
+    double delta;      /* reliable update when |r| < delta * max|r| since the last
+                          one (default 0.1; ignored for plain FP64 CG)                */
+    int max_iter;      /* default 100000                                              */
+    int block_iters;   /* CG iterations per graph launch (default 16)                 */
+    unsigned flags;    /* SQ_CG_* */
+    void *stream;      /* cudaStream_t, NULL = context stream                         */
+} sq_cg_opts;
+
+typedef struct {
+    int status;            /* sq_status of this solve                          */
+    int iterations;
+    int reliable_updates;  /* FP64 true-residual recomputations                */
+    double true_residual;  /* |b - A x| / |b|, FP64, computed on the GPU       */
+    double seconds;        /* wall time of the solve (host clock)              */
+    double gflops;         /* 2364 flop per even site per iteration            */
+} sq_cg_stats;
+
+typedef struct {
+    uint64_t submitted, completed, rejected;
+    int queued, running;
+    double p50_ms, p99_ms, mean_ms;   /* submit -> result ready, completed requests */
+    double solves_per_s;              /* completed / (last completion - first submit) */
+    size_t hbm_in_use, hbm_budget;
+} sq_serve_stats;
+
+/* ---- context -------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the context may hold (gauge fields + solver workspaces); 0 = 90% of
+ * the device's free memory.  Returns SQ_ERR_CUDA without a usable device. */
+int sq_create(sq_ctx **out, int device, size_t hbm_budget_bytes);
+int sq_destroy(sq_ctx *ctx);
+const char *sq_strerror(int status);
+void sq_cg_opts_default(sq_cg_opts *opts);
+
+/* Number of kernel launches the context has issued (graph launches count each
+ * kernel node), for launch accounting. */
+uint64_t sq_kernel_launches(const sq_ctx *ctx);
+
+/* ---- gauge field ---------------------------------------------------------- */
+
+/* Load fat and long links (layout above) and pack them into the device forms
+ * used by the Dslash: for each output parity, per site, the 16 hop matrices
+ * F_mu(x), F_mu(x-mu)^dag, L_mu(x), L_mu(x-3mu)^dag, stored site-major in
+ * 16-byte planes, in FP64, FP32 and 16-bit (global scale per link kind), with
+ * the long links also in 12-real form (third row rebuilt as
+ * conj(row0 x row1)/s, s the common scale of the long links, found from
+ * det L = s^3 and checked on every link).  One-time; the caller may free the
+ * inputs on return.  The paper's links come from the MILC asqtad ensemble
+ * (Sec. 2, Fig. 1); any fat/long pair in this layout is accepted. */
+int gauge_load(sq_ctx *ctx, const int dims[4], const double *fat, const double *lng,
+               unsigned flags, int *gauge_id);
+int gauge_free(sq_ctx *ctx, int gauge_id);
+
+/* Bytes of one packed parity-half vector of `prec` for this gauge field's
+ * lattice, and the plane stride in sites. */
+int sq_spinor_bytes(sq_ctx *ctx, int gauge_id, int prec, size_t *bytes, int *stride);
+
+/* Canonical (complex128) <-> packed device vector of one parity.  Both
+ * pointers are device pointers; asynchronous on `stream`. */
+int sq_pack_spinor(sq_ctx *ctx, int gauge_id, int prec, const double *canon_dev,
+                   void *packed_dev, void *stream);
+int sq_unpack_spinor(sq_ctx *ctx, int gauge_id, int prec, const void *packed_dev,
+                     double *canon_dev, void *stream);
+
+/* ---- operators ------------------------------------------------------------ */
+
+/* out = D_{p,1-p} in: the asqtad Dslash from parity 1-out_parity to parity
+ * out_parity (the 16 SU(3) mat-vecs per site above), in `prec` with long
+ * links in `long_recon` (18 or 12) form.  in/out are packed device vectors
+ * (distinct buffers).  Asynchronous on `stream`; no host synchronisation. */
+int dslash_apply(sq_ctx *ctx, int gauge_id, int out_parity, int prec, int long_recon,
+                 const void *in_dev, void *out_dev, void *stream);
+
+/* out = (m^2 - D_eo D_oe) in on the even parity: the CG operator, as the two
+ * Dslash kernels the solver runs (the second with the m^2 epilogue).  Uses a
+ * context-owned odd-parity temporary. */
+int mdagm_apply(sq_ctx *ctx, int gauge_id, int prec, int long_recon, double mass,
+                const void *in_dev, void *out_dev, void *stream);
+
+/* ---- solvers -------------------------------------------------------------- */
+
+/* Solve (m^2 - D_eo D_oe) x = b to |b - A x| / |b| <= tol: CG in the sloppy
+ * precision opts->precision with FP64 reliable updates (the FP64 true
+ * residual is recomputed, and CG restarted from it, whenever |r| falls below
+ * delta times its maximum since the previous update, and before returning);
+ * the solution accumulates in FP64.  With precision SQ_PREC_F64 it is plain
+ * FP64 CG.  This is the paper's mixed-precision CG (Sec. 2: "most of the
+ * calculations are performed in single precision"; Sec. 3).  src/x are
+ * canonical even-parity vectors, host pointers unless SQ_CG_DEVICE_PTRS.
+ * opts may be NULL (defaults).  stats may be NULL. */
+int cg_solve(sq_ctx *ctx, int gauge_id, const double *src_even, double mass, double tol,
+             const sq_cg_opts *opts, double *x_even, sq_cg_stats *stats);
+
+/* Batched solve of nrhs systems (m_j^2 - D_eo D_oe) x_j = b_j on one gauge
+ * field: every Dslash streams each link once for all right-hand sides.
+ * src/x: nrhs canonical vectors back to back; masses: nrhs values; stats:
+ * nrhs entries (may be NULL).  Each system follows cg_solve's algorithm and
+ * stops on its own. */
+int cg_solve_multi(sq_ctx *ctx, int gauge_id, int nrhs, const double *src,
+                   const double *masses, double tol, const sq_cg_opts *opts,
+                   double *x, sq_cg_stats *stats);
+
+/* Multi-shift CG: (m_i^2 - D_eo D_oe) x_i = b for nshift masses from one
+ * Krylov space (Jegerlehner's shifted recurrences), run in the sloppy
+ * precision to max(tol, 1e-5 for FP32 / 1e-3 for 16-bit), then refined per
+ * shift by the batched mixed-precision CG above started from the shifted
+ * solutions.  x: nshift canonical vectors; stats: nshift entries (may be NULL). */
+int cg_solve_multishift(sq_ctx *ctx, int gauge_id, const double *src, int nshift,
+                        const double *masses, double tol, const sq_cg_opts *opts,
+                        double *x, sq_cg_stats *stats);
+
+/* ---- serving -------------------------------------------------------------- */
+
+/* Continuous-batching request loop.  serve_submit copies the host source and
+ * queues one solve; a scheduler thread admits queued requests into free slots
+ * of the running batched CG of their gauge field (at iteration-block
+ * boundaries) while the HBM budget allows, runs the batches of all gauge
+ * fields concurrently on separate streams and retires converged slots.
+ * Options of a served solve: sq_cg_opts defaults (FP32 sloppy, 18-real). */
+int serve_submit(sq_ctx *ctx, int gauge_id, const double *src_even, double mass, double tol,
+                 uint64_t *ticket);
+
+/* Wait up to timeout_us (0: do not wait; <0: forever) for a ticket; on
+ * completion copy x into x_even (host, may be NULL) and stats, release the
+ * ticket and return the solve's status.  SQ_PENDING if not yet done;
+ * SQ_ERR_NOTFOUND for an unknown or already released ticket. */
+int serve_poll(sq_ctx *ctx, uint64_t ticket, double *x_even, sq_cg_stats *stats,
+               int timeout_us);
+
+/* Cancel a queued or running request (its ticket then polls SQ_ERR_NOTFOUND). */
+int serve_cancel(sq_ctx *ctx, uint64_t ticket);
+
+/* Serving counters and latency percentiles since the context was created (or
+ * the last reset). */
+int serve_stats(sq_ctx *ctx, sq_serve_stats *stats, int reset);
+
+/* Slots per gauge-field batch (default 8, at most 16); set before submitting. */
+int serve_configure(sq_ctx *ctx, int slots_per_batch, int block_iters);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SQ_H */

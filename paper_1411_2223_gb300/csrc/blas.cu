@@ -1,0 +1,256 @@
+// CG vector kernels (fused axpy / xpay with FP64 norms) and the canonical <->
+// packed colour-vector conversions.  All are bandwidth-bound streaming
+// kernels: one thread per site, 16-byte accesses, one right-hand side per
+// grid row (blockIdx.y).
+#include "sq_device.cuh"
+#include "cg_finish.cuh"
+#include "sq_kernels.h"
+
+namespace sq {
+
+namespace {
+
+__device__ __forceinline__ bool running(const SlotState *s) { return s->status == SLOT_RUNNING; }
+
+__device__ __forceinline__ bool any_running(const SlotState *s, int n) {
+  bool any = false;
+  for (int r = 0; r < n; ++r) any |= running(s + r);
+  return any;
+}
+
+// x64 += alpha p ; r -= alpha Ap ; partial |r|^2 ; last block: finish_update
+template <int S>
+__global__ void __launch_bounds__(256) cg_update_kernel(VecArgs a) {
+  using R = typename SpinorIO<S>::R;
+  if (!any_running(a.slots, a.nrhs)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  const int St = a.g.stride;
+  SlotState *s = a.slots + r;
+  double val[1] = {0.0};
+  if (i < a.g.vh && running(s)) {
+    const double alpha = s->alpha;
+    Vec3<R> p = SpinorIO<S>::load(a.p + r * a.fb, St, i);
+    Vec3<R> ap = SpinorIO<S>::load(a.ap + r * a.fb, St, i);
+    Vec3<R> rv = SpinorIO<S>::load(a.r + r * a.fb, St, i);
+    Vec3<double> x = SpinorIO<PREC_F64>::load(a.x64 + r * a.f64_fb, St, i);
+    const R al = (R)alpha;
+    R n2 = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      x.c[c].x = fma(alpha, (double)p.c[c].x, x.c[c].x);
+      x.c[c].y = fma(alpha, (double)p.c[c].y, x.c[c].y);
+      rv.c[c].x = fma(-al, ap.c[c].x, rv.c[c].x);
+      rv.c[c].y = fma(-al, ap.c[c].y, rv.c[c].y);
+      n2 = fma(rv.c[c].x, rv.c[c].x, fma(rv.c[c].y, rv.c[c].y, n2));
+    }
+    SpinorIO<PREC_F64>::store(a.x64 + r * a.f64_fb, St, i, x);
+    SpinorIO<S>::store(a.r + r * a.fb, St, i, rv);
+    val[0] = (double)n2;
+  }
+  __shared__ double smem[8];
+  chunk_reduce<1>(val, smem, a.partial + (size_t)r * a.g.nchunks, a.g.nchunks);
+  if (last_block_arrived(a.counter, gridDim.x * gridDim.y)) {
+    __shared__ double red[32];
+    for (int k = 0; k < a.nrhs; ++k) {
+      if (!running(a.slots + k)) continue;
+      double rr = block_sum_fixed(a.partial + (size_t)k * a.g.nchunks, a.g.nchunks, red);
+      if (threadIdx.x == 0) finish_update(a.slots + k, rr);
+    }
+    if (threadIdx.x == 0) *a.counter = 0;
+  }
+}
+
+// p = a r + beta p (a complex, 1 except right after a reliable update)
+template <int S>
+__global__ void __launch_bounds__(256) cg_xpay_kernel(VecArgs a) {
+  using R = typename SpinorIO<S>::R;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  const SlotState *s = a.slots + r;
+  if (i >= a.g.vh || !running(s)) return;
+  const int St = a.g.stride;
+  const R are = (R)s->a_re, aim = (R)s->a_im, beta = (R)s->beta;
+  Vec3<R> rv = SpinorIO<S>::load(a.r + r * a.fb, St, i);
+  Vec3<R> p = SpinorIO<S>::load(a.p + r * a.fb, St, i);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R px = fma(are, rv.c[c].x, fma(-aim, rv.c[c].y, beta * p.c[c].x));
+    R py = fma(are, rv.c[c].y, fma(aim, rv.c[c].x, beta * p.c[c].y));
+    p.c[c].x = px;
+    p.c[c].y = py;
+  }
+  SpinorIO<S>::store(a.p + r * a.fb, St, i, p);
+}
+
+// Start of a solve: r = b (sloppy), p = r, x64 = 0; or with an initial guess
+// p = 0 and a pending FP64 residual.  Partial |b|^2; last block: finish_init.
+template <int S>
+__global__ void __launch_bounds__(256) cg_init_kernel(VecArgs a, int guess) {
+  using R = typename SpinorIO<S>::R;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  const int St = a.g.stride;
+  SlotState *s = a.slots + r;
+  const bool act = running(s);
+  double val[1] = {0.0};
+  if (i < a.g.vh && act) {
+    Vec3<double> b = SpinorIO<PREC_F64>::load(a.b64 + r * a.f64_fb, St, i);
+    double n2 = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) n2 = fma(b.c[c].x, b.c[c].x, fma(b.c[c].y, b.c[c].y, n2));
+    val[0] = n2;
+    if (guess) {
+      Vec3<R> z;
+      zero(z);
+      SpinorIO<S>::store(a.p + r * a.fb, St, i, z);
+    } else {
+      Vec3<R> rv = convert<R>(b);
+      SpinorIO<S>::store(a.r + r * a.fb, St, i, rv);
+      SpinorIO<S>::store(a.p + r * a.fb, St, i, rv);
+      Vec3<double> z;
+      zero(z);
+      SpinorIO<PREC_F64>::store(a.x64 + r * a.f64_fb, St, i, z);
+    }
+  }
+  __shared__ double smem[8];
+  chunk_reduce<1>(val, smem, a.partial + (size_t)r * a.g.nchunks, a.g.nchunks);
+  if (last_block_arrived(a.counter, gridDim.x * gridDim.y)) {
+    __shared__ double red[32];
+    for (int k = 0; k < a.nrhs; ++k) {
+      if (!running(a.slots + k)) continue;
+      double b2 = block_sum_fixed(a.partial + (size_t)k * a.g.nchunks, a.g.nchunks, red);
+      if (threadIdx.x == 0) {
+        finish_init(a.slots + k, b2);
+        if (guess && a.slots[k].status == SLOT_RUNNING) a.slots[k].ru_pending = 1;
+      }
+    }
+    if (threadIdx.x == 0) *a.counter = 0;
+  }
+}
+
+// canonical [i][colour] complex128 -> packed precision P (nrhs fields)
+template <int P>
+__global__ void pack_kernel(Geom g, const double2 *canon, size_t canon_fe, char *out,
+                            size_t out_fb) {
+  using R = typename SpinorIO<P>::R;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (i >= g.vh) return;
+  const double2 *c = canon + r * canon_fe + (size_t)3 * i;
+  Vec3<double> v;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v.c[k] = c[k];
+  SpinorIO<P>::store(out + r * out_fb, g.stride, i, convert<R>(v));
+}
+
+template <int P>
+__global__ void unpack_kernel(Geom g, const char *in, size_t in_fb, double2 *canon,
+                              size_t canon_fe) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (i >= g.vh) return;
+  auto v = SpinorIO<P>::load(in + r * in_fb, g.stride, i);
+  double2 *c = canon + r * canon_fe + (size_t)3 * i;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) c[k] = make_double2((double)v.c[k].x, (double)v.c[k].y);
+}
+
+// x64 (packed FP64) <-> canonical for the solution / source of a solve
+template <int P>
+__global__ void convert_kernel(Geom g, const char *in, size_t in_fb, char *out, size_t out_fb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (i >= g.vh) return;
+  auto v = SpinorIO<PREC_F64>::load(in + r * in_fb, g.stride, i);
+  SpinorIO<P>::store(out + r * out_fb, g.stride, i, convert<typename SpinorIO<P>::R>(v));
+}
+
+inline dim3 grid_for(const Geom &g, int block, int nrhs) {
+  return dim3((g.vh + block - 1) / block, nrhs);
+}
+
+}  // namespace
+
+int launch_cg_update(int prec, const VecArgs &a, cudaStream_t st) {
+  if (a.g.vh <= 0) return 0;
+  dim3 grid = grid_for(a.g, 256, a.nrhs);
+  switch (prec) {
+    case PREC_F64: cg_update_kernel<PREC_F64><<<grid, 256, 0, st>>>(a); break;
+    case PREC_F32: cg_update_kernel<PREC_F32><<<grid, 256, 0, st>>>(a); break;
+    case PREC_I16: cg_update_kernel<PREC_I16><<<grid, 256, 0, st>>>(a); break;
+    default: return -1;
+  }
+  return 0;
+}
+
+int launch_cg_xpay(int prec, const VecArgs &a, cudaStream_t st) {
+  if (a.g.vh <= 0) return 0;
+  dim3 grid = grid_for(a.g, 256, a.nrhs);
+  switch (prec) {
+    case PREC_F64: cg_xpay_kernel<PREC_F64><<<grid, 256, 0, st>>>(a); break;
+    case PREC_F32: cg_xpay_kernel<PREC_F32><<<grid, 256, 0, st>>>(a); break;
+    case PREC_I16: cg_xpay_kernel<PREC_I16><<<grid, 256, 0, st>>>(a); break;
+    default: return -1;
+  }
+  return 0;
+}
+
+int launch_cg_init(int prec, const VecArgs &a, int guess, cudaStream_t st) {
+  if (a.g.vh <= 0) return 0;
+  dim3 grid = grid_for(a.g, 256, a.nrhs);
+  switch (prec) {
+    case PREC_F64: cg_init_kernel<PREC_F64><<<grid, 256, 0, st>>>(a, guess); break;
+    case PREC_F32: cg_init_kernel<PREC_F32><<<grid, 256, 0, st>>>(a, guess); break;
+    case PREC_I16: cg_init_kernel<PREC_I16><<<grid, 256, 0, st>>>(a, guess); break;
+    default: return -1;
+  }
+  return 0;
+}
+
+int launch_pack(int prec, const Geom &g, const double *canon, size_t canon_elems, void *out,
+                size_t out_fb, int nrhs, cudaStream_t st) {
+  if (g.vh <= 0) return 0;
+  dim3 grid = grid_for(g, 256, nrhs);
+  const double2 *c = reinterpret_cast<const double2 *>(canon);
+  char *o = static_cast<char *>(out);
+  switch (prec) {
+    case PREC_F64: pack_kernel<PREC_F64><<<grid, 256, 0, st>>>(g, c, canon_elems, o, out_fb); break;
+    case PREC_F32: pack_kernel<PREC_F32><<<grid, 256, 0, st>>>(g, c, canon_elems, o, out_fb); break;
+    case PREC_I16: pack_kernel<PREC_I16><<<grid, 256, 0, st>>>(g, c, canon_elems, o, out_fb); break;
+    default: return -1;
+  }
+  return 0;
+}
+
+int launch_unpack(int prec, const Geom &g, const void *in, size_t in_fb, double *canon,
+                  size_t canon_elems, int nrhs, cudaStream_t st) {
+  if (g.vh <= 0) return 0;
+  dim3 grid = grid_for(g, 256, nrhs);
+  double2 *c = reinterpret_cast<double2 *>(canon);
+  const char *p = static_cast<const char *>(in);
+  switch (prec) {
+    case PREC_F64: unpack_kernel<PREC_F64><<<grid, 256, 0, st>>>(g, p, in_fb, c, canon_elems); break;
+    case PREC_F32: unpack_kernel<PREC_F32><<<grid, 256, 0, st>>>(g, p, in_fb, c, canon_elems); break;
+    case PREC_I16: unpack_kernel<PREC_I16><<<grid, 256, 0, st>>>(g, p, in_fb, c, canon_elems); break;
+    default: return -1;
+  }
+  return 0;
+}
+
+int launch_convert_from_f64(int prec, const Geom &g, const void *in, size_t in_fb, void *out,
+                            size_t out_fb, int nrhs, cudaStream_t st) {
+  if (g.vh <= 0) return 0;
+  dim3 grid = grid_for(g, 256, nrhs);
+  const char *p = static_cast<const char *>(in);
+  char *o = static_cast<char *>(out);
+  switch (prec) {
+    case PREC_F64: convert_kernel<PREC_F64><<<grid, 256, 0, st>>>(g, p, in_fb, o, out_fb); break;
+    case PREC_F32: convert_kernel<PREC_F32><<<grid, 256, 0, st>>>(g, p, in_fb, o, out_fb); break;
+    case PREC_I16: convert_kernel<PREC_I16><<<grid, 256, 0, st>>>(g, p, in_fb, o, out_fb); break;
+    default: return -1;
+  }
+  return 0;
+}
+
+}  // namespace sq

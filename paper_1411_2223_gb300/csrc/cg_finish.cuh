@@ -1,0 +1,96 @@
+// Scalar steps of the CG recurrences, run by one thread of the last block of
+// each reduction kernel so that an iteration needs no host round trip.
+//
+// CG on A x = b (Hestenes-Stiefel): alpha = rr / <p, A p>, x += alpha p,
+// r -= alpha A p, beta = rr_new / rr, p = r + beta p.  The mixed-precision
+// variant (the paper's "most of the calculations in single precision", Sec. 2)
+// keeps x in FP64 and recomputes the true residual b - A x in FP64 whenever
+// |r| drops below delta * max|r| since the last update, when the recursion
+// claims convergence, and at max_iter (reliable updates).  After such an
+// update the old direction p is made orthogonal to the new residual,
+// p <- p - (<r, p> / |r|^2) r, before p = r + beta p.
+#pragma once
+
+#include "sq_types.h"
+
+namespace sq {
+
+__device__ __forceinline__ void finish_init(SlotState *s, double b2) {
+  s->b2 = b2;
+  s->tol2b2 = s->tol2 * b2;
+  s->rr = b2;
+  s->maxr = sqrt(b2);
+  s->iter = 0;
+  s->n_ru = 0;
+  s->alpha = 0;
+  s->beta = 0;
+  s->a_re = 1;
+  s->a_im = 0;
+  if (!isfinite(b2)) {
+    s->status = SLOT_NONFINITE;
+    s->ru_pending = 0;
+  } else if (b2 == 0.0) {
+    s->status = SLOT_CONVERGED;
+    s->rr_true = 0;
+    s->ru_pending = 0;
+  }
+}
+
+__device__ __forceinline__ void finish_alpha(SlotState *s, double pap) {
+  if (!isfinite(pap)) {
+    s->status = SLOT_NONFINITE;
+  } else if (pap > 0.0) {
+    s->alpha = s->rr / pap;
+  } else {  // p vanished: only a true-residual check can decide
+    s->alpha = 0.0;
+    s->ru_pending = 1;
+  }
+}
+
+__device__ __forceinline__ void finish_update(SlotState *s, double rr_new) {
+  s->iter += 1;
+  if (!isfinite(rr_new)) {
+    s->status = SLOT_NONFINITE;
+    return;
+  }
+  double rn = sqrt(rr_new);
+  bool ru = s->ru_pending || rr_new <= s->tol2b2 || rn < s->delta * s->maxr ||
+            s->iter >= s->max_iter;
+  if (ru) {
+    s->ru_pending = 1;  // beta and rr come from the FP64 residual
+    return;
+  }
+  s->beta = rr_new / s->rr;
+  s->a_re = 1.0;
+  s->a_im = 0.0;
+  s->rr = rr_new;
+  s->maxr = fmax(s->maxr, rn);
+}
+
+// rr_true = |b - A x|^2, (rp_re, rp_im) = <r_true, p>
+__device__ __forceinline__ void finish_reliable_update(SlotState *s, double rr_true,
+                                                       double rp_re, double rp_im) {
+  s->ru_pending = 0;
+  s->n_ru += 1;
+  s->rr_true = rr_true;
+  if (!isfinite(rr_true)) {
+    s->status = SLOT_NONFINITE;
+    return;
+  }
+  if (rr_true <= s->tol2b2) {
+    s->status = SLOT_CONVERGED;
+    return;
+  }
+  if (s->iter >= s->max_iter) {
+    s->status = SLOT_MAXITER;
+    return;
+  }
+  double beta = (s->rr > 0.0) ? rr_true / s->rr : 0.0;
+  s->beta = beta;
+  s->a_re = 1.0 - beta * rp_re / rr_true;
+  s->a_im = -beta * rp_im / rr_true;
+  s->rr = rr_true;
+  s->maxr = sqrt(rr_true);
+}
+
+}  // namespace sq

@@ -1,0 +1,275 @@
+// The asqtad even-odd Dslash kernel family.
+//
+//   (D psi)(x) = 1/2 sum_mu eta_mu(x) [ F_mu(x) psi(x+mu) - F_mu(x-mu)^dag psi(x-mu)
+//                                      + L_mu(x) psi(x+3mu) - L_mu(x-3mu)^dag psi(x-3mu) ]
+//
+// for the output sites x of one parity (the paper's CG inverter on the asqtad
+// lattice, Sec. 2 / Fig. 1, spends its time in this operator).  One thread
+// per output site; each thread reads the site's 16 hop matrices once (16-byte
+// streaming loads, site-major planes) and applies them to NR right-hand
+// sides.  The neighbours' colour vectors are gathered through L1/L2 (the
+// input field of one parity is small enough to stay in L2).
+//
+// Epilogues:
+//   MODE_PLAIN  out = D in
+//   MODE_MDAGM  out = m^2 p - D in               (second Dslash of A = m^2 - D_eo D_oe)
+//               + per-chunk partials of Re<p, out>, and the last block sets
+//               alpha = rr / <p, Ap> for every running system
+//   MODE_RESID  r = b - (m^2 x - D in), FP64     (reliable update: true residual)
+//               written in the sloppy precision OUTP, + partials of |r|^2
+//               and <r, p_sloppy>; the last block finishes the update
+#pragma once
+
+#include "sq_device.cuh"
+#include "cg_finish.cuh"
+
+namespace sq {
+
+enum DslashMode { MODE_PLAIN = 0, MODE_MDAGM = 1, MODE_RESID = 2 };
+enum Gate { GATE_NONE = 0, GATE_RUNNING = 1, GATE_RU = 2 };
+
+struct DslashArgs {
+  Geom g;
+  int out_parity;
+  const char *links;          // link planes of the output parity (this precision/recon)
+  LinkScales ls;
+  const char *in;             // nrhs input fields (parity 1 - out_parity)
+  char *out;                  // nrhs output fields
+  size_t in_fb, out_fb;       // bytes between consecutive rhs fields
+  int nrhs;
+  double m2_const;            // MDAGM without slots: the mass^2
+  // MDAGM: p (output parity, same precision as in)
+  const char *p;
+  size_t p_fb;
+  // RESID: FP64 x and b, sloppy p
+  const char *x64, *b64;
+  size_t f64_fb;
+  const char *ps;
+  size_t ps_fb;
+  SlotState *slots;           // nullptr: no CG state (operator application only)
+  double *partial;            // [value][rhs][chunk]
+  unsigned *counter;
+  int gate;
+};
+
+template <int PREC> struct AccumType { using R = float; };
+template <> struct AccumType<PREC_F64> { using R = double; };
+
+__device__ __forceinline__ bool slot_active(const SlotState *s, int gate) {
+  if (gate == GATE_RUNNING) return s->status == SLOT_RUNNING;
+  if (gate == GATE_RU) return s->ru_pending != 0;
+  return true;
+}
+
+// Colour vector of hop neighbour n for rhs field `f`, multiplied by `scale`
+// (boundary sign, and for 16-bit data the code scales).
+template <int PREC, typename R>
+__device__ __forceinline__ Vec3<R> gather(const char *f, int S, int n, float scale) {
+  if constexpr (PREC == PREC_I16) {
+    float s;
+    Vec3<float> v = SpinorIO<PREC_I16>::load_codes(f, n, s);
+    s *= scale;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { v.c[c].x *= s; v.c[c].y *= s; }
+    return v;
+  } else {
+    Vec3<R> v = SpinorIO<PREC>::load(f, S, n);
+    if (scale < 0.f) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { v.c[c].x = -v.c[c].x; v.c[c].y = -v.c[c].y; }
+    }
+    return v;
+  }
+}
+
+// acc -= M v
+template <typename R>
+__device__ __forceinline__ void mat_vec_sub(Vec3<R> &acc, const Mat3<R> &m, const Vec3<R> &v) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc.c[r].x = fma(-m.e[3 * r + c].x, v.c[c].x, acc.c[r].x);
+      acc.c[r].x = fma(m.e[3 * r + c].y, v.c[c].y, acc.c[r].x);
+      acc.c[r].y = fma(-m.e[3 * r + c].x, v.c[c].y, acc.c[r].y);
+      acc.c[r].y = fma(-m.e[3 * r + c].y, v.c[c].x, acc.c[r].y);
+    }
+  }
+}
+
+template <int PREC, int RECON, int NR, int MODE, int OUTP>
+__global__ void __launch_bounds__(512)
+dslash_kernel(const DslashArgs a) {
+  using R = typename AccumType<PREC>::R;
+  const Geom &g = a.g;
+  const int S = g.stride;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r0 = blockIdx.y * NR;
+
+  // Gate: the decision is the same in every block (slot state only changes in
+  // the last block of a reduction kernel, after all blocks have read it).
+  bool active[NR];
+  bool any_here = false;
+  if (a.slots != nullptr && a.gate != GATE_NONE) {
+    bool any = false;
+    for (int r = 0; r < a.nrhs; ++r) any |= slot_active(a.slots + r, a.gate);
+    if (!any) return;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      active[r] = (r0 + r < a.nrhs) && slot_active(a.slots + r0 + r, a.gate);
+      any_here |= active[r];
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) active[r] = (r0 + r < a.nrhs);
+    any_here = true;
+  }
+  const bool valid = (i < g.vh) && any_here;
+
+  Vec3<R> acc[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) zero(acc[r]);
+
+  if (valid) {
+    const SiteCoords sc = site_coords(g, a.out_parity, i);
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+      Mat3<R> m[4];
+      LinkIO<PREC, RECON>::load(a.links, S, i, mu, a.ls, m);
+      float sg[4];
+      int nb[4];
+      nb[0] = hop_index(g, sc, mu, +1, sg[0]);
+      nb[1] = hop_index(g, sc, mu, -1, sg[1]);
+      nb[2] = hop_index(g, sc, mu, +3, sg[2]);
+      nb[3] = hop_index(g, sc, mu, -3, sg[3]);
+      if constexpr (PREC == PREC_I16) {
+        sg[0] *= a.ls.fat_k; sg[1] *= a.ls.fat_k;
+        sg[2] *= a.ls.long_k; sg[3] *= a.ls.long_k;
+      }
+      const float eta = eta_sign(sc, mu);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (!active[r]) continue;
+        const char *f = a.in + (size_t)(r0 + r) * a.in_fb;
+        Vec3<R> t;
+        zero(t);
+        Vec3<R> v;
+        v = gather<PREC, R>(f, S, nb[0], sg[0]);
+        mat_vec_acc(t, m[0], v);
+        v = gather<PREC, R>(f, S, nb[1], sg[1]);
+        mat_vec_sub(t, m[1], v);
+        v = gather<PREC, R>(f, S, nb[2], sg[2]);
+        mat_vec_acc(t, m[2], v);
+        v = gather<PREC, R>(f, S, nb[3], sg[3]);
+        mat_vec_sub(t, m[3], v);
+        if (eta > 0.f) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) { acc[r].c[c].x += t.c[c].x; acc[r].c[c].y += t.c[c].y; }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) { acc[r].c[c].x -= t.c[c].x; acc[r].c[c].y -= t.c[c].y; }
+        }
+      }
+    }
+  }
+
+  if constexpr (MODE == MODE_PLAIN) {
+    if (valid) {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (!active[r]) continue;
+        Vec3<R> o;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { o.c[c].x = R(0.5) * acc[r].c[c].x; o.c[c].y = R(0.5) * acc[r].c[c].y; }
+        SpinorIO<PREC>::store(a.out + (size_t)(r0 + r) * a.out_fb, S, i, o);
+      }
+    }
+  } else if constexpr (MODE == MODE_MDAGM) {
+    // Ap = m^2 p - 1/2 acc ; partial Re<p, Ap>
+    double dot[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      dot[r] = 0.0;
+      if (valid && active[r]) {
+        const R m2 = (R)(a.slots ? a.slots[r0 + r].m2 : a.m2_const);
+        Vec3<R> p = SpinorIO<PREC>::load(a.p + (size_t)(r0 + r) * a.p_fb, S, i);
+        Vec3<R> o;
+        R d = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          o.c[c].x = fma(m2, p.c[c].x, R(-0.5) * acc[r].c[c].x);
+          o.c[c].y = fma(m2, p.c[c].y, R(-0.5) * acc[r].c[c].y);
+          d = fma(p.c[c].x, o.c[c].x, d);
+          d = fma(p.c[c].y, o.c[c].y, d);
+        }
+        SpinorIO<PREC>::store(a.out + (size_t)(r0 + r) * a.out_fb, S, i, o);
+        dot[r] = (double)d;
+      }
+    }
+    if (a.slots != nullptr && a.partial != nullptr) {
+      __shared__ double smem[NR * 16];
+      chunk_reduce<NR>(dot, smem, a.partial + (size_t)r0 * g.nchunks, g.nchunks,
+                       min(NR, a.nrhs - r0));
+      if (last_block_arrived(a.counter, gridDim.x * gridDim.y)) {
+        __shared__ double red[32];
+        for (int r = 0; r < a.nrhs; ++r) {
+          if (!slot_active(a.slots + r, a.gate)) continue;
+          double pap = block_sum_fixed(a.partial + (size_t)r * g.nchunks, g.nchunks, red);
+          if (threadIdx.x == 0) finish_alpha(a.slots + r, pap);
+        }
+        if (threadIdx.x == 0) *a.counter = 0;
+      }
+    }
+  } else {  // MODE_RESID (PREC == F64)
+    double val[3][NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      val[0][r] = val[1][r] = val[2][r] = 0.0;
+      if (valid && active[r]) {
+        const double m2 = a.slots[r0 + r].m2;
+        Vec3<double> x = SpinorIO<PREC_F64>::load(a.x64 + (size_t)(r0 + r) * a.f64_fb, S, i);
+        Vec3<double> b = SpinorIO<PREC_F64>::load(a.b64 + (size_t)(r0 + r) * a.f64_fb, S, i);
+        Vec3<double> rr;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          rr.c[c].x = b.c[c].x - fma(m2, x.c[c].x, -0.5 * (double)acc[r].c[c].x);
+          rr.c[c].y = b.c[c].y - fma(m2, x.c[c].y, -0.5 * (double)acc[r].c[c].y);
+        }
+        using RO = typename SpinorIO<OUTP>::R;
+        Vec3<RO> p = SpinorIO<OUTP>::load(a.ps + (size_t)(r0 + r) * a.ps_fb, S, i);
+        double n2 = 0, pre = 0, pim = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          n2 = fma(rr.c[c].x, rr.c[c].x, fma(rr.c[c].y, rr.c[c].y, n2));
+          // <r, p> = sum conj(r) p
+          pre = fma(rr.c[c].x, (double)p.c[c].x, fma(rr.c[c].y, (double)p.c[c].y, pre));
+          pim = fma(rr.c[c].x, (double)p.c[c].y, fma(-rr.c[c].y, (double)p.c[c].x, pim));
+        }
+        SpinorIO<OUTP>::store(a.out + (size_t)(r0 + r) * a.out_fb, S, i, convert<RO>(rr));
+        val[0][r] = n2; val[1][r] = pre; val[2][r] = pim;
+      }
+    }
+    __shared__ double smem[NR * 16];
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+      chunk_reduce<NR>(val[v], smem, a.partial + ((size_t)v * a.nrhs + r0) * g.nchunks, g.nchunks,
+                       min(NR, a.nrhs - r0));
+    if (last_block_arrived(a.counter, gridDim.x * gridDim.y)) {
+      __shared__ double red[32];
+      for (int r = 0; r < a.nrhs; ++r) {
+        if (!slot_active(a.slots + r, GATE_RU)) continue;
+        double s0 = block_sum_fixed(a.partial + ((size_t)0 * a.nrhs + r) * g.nchunks, g.nchunks, red);
+        double s1 = block_sum_fixed(a.partial + ((size_t)1 * a.nrhs + r) * g.nchunks, g.nchunks, red);
+        double s2 = block_sum_fixed(a.partial + ((size_t)2 * a.nrhs + r) * g.nchunks, g.nchunks, red);
+        if (threadIdx.x == 0) finish_reliable_update(a.slots + r, s0, s1, s2);
+      }
+      if (threadIdx.x == 0) *a.counter = 0;
+    }
+  }
+}
+
+// Host-side launcher (defined per precision in dslash_*.cu).
+int launch_dslash(int prec, int recon, int nr, int mode, int outp, const DslashArgs &a,
+                  int block, cudaStream_t stream);
+
+}  // namespace sq

@@ -1,0 +1,36 @@
+// Host-side launchers of the library's kernels (all asynchronous).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sq_types.h"
+
+namespace sq {
+
+// Arguments of the CG vector kernels (nrhs fields per vector, fb bytes apart).
+struct VecArgs {
+  Geom g;
+  int nrhs;
+  char *x64;          // FP64 solution fields
+  const char *b64;    // FP64 sources
+  size_t f64_fb;
+  char *r, *p, *ap;   // sloppy-precision fields
+  size_t fb;
+  SlotState *slots;
+  double *partial;
+  unsigned *counter;
+};
+
+int launch_cg_update(int prec, const VecArgs &a, cudaStream_t st);
+int launch_cg_xpay(int prec, const VecArgs &a, cudaStream_t st);
+int launch_cg_init(int prec, const VecArgs &a, int guess, cudaStream_t st);
+
+// canonical complex128 [i][colour] (nrhs fields, canon_elems complex apart)
+int launch_pack(int prec, const Geom &g, const double *canon, size_t canon_elems, void *out,
+                size_t out_fb, int nrhs, cudaStream_t st);
+int launch_unpack(int prec, const Geom &g, const void *in, size_t in_fb, double *canon,
+                  size_t canon_elems, int nrhs, cudaStream_t st);
+int launch_convert_from_f64(int prec, const Geom &g, const void *in, size_t in_fb, void *out,
+                            size_t out_fb, int nrhs, cudaStream_t st);
+
+}  // namespace sq

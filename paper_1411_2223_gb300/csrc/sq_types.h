@@ -1,0 +1,57 @@
+// Types shared by host and device code of the asqtad CG library.
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+namespace sq {
+
+enum Prec { PREC_F64 = 0, PREC_F32 = 1, PREC_I16 = 2 };
+
+// Lattice geometry of one gauge field (passed to kernels by value).
+struct Geom {
+  int L[4];            // Lx, Ly, Lz, Lt (all even)
+  int st[4];           // lexicographic strides 1, Lx, Lx*Ly, Lx*Ly*Lz
+  int lxh;             // Lx / 2
+  int vh;              // sites per parity
+  int stride;          // plane stride in sites (vh rounded up to 64)
+  int nchunks;         // ceil(vh / CHUNK)
+  int t_antiperiodic;  // 1: hops wrapping around t pick up -1
+};
+
+// Bytes of one packed parity-half colour vector.
+inline size_t spinor_bytes(int prec, int stride) {
+  return (size_t)stride * (prec == PREC_F64 ? 48 : prec == PREC_F32 ? 24 : 16);
+}
+
+// Per right-hand-side CG state, resident on the device.  The reduction
+// kernels' last block updates it, so no host round trip sits inside an
+// iteration.
+enum SlotStatus {
+  SLOT_RUNNING = 0,
+  SLOT_CONVERGED = 1,
+  SLOT_MAXITER = 2,
+  SLOT_NONFINITE = 3,
+  SLOT_IDLE = 4,  // no system in this slot
+};
+
+struct SlotState {
+  double m2;        // mass^2 of this system
+  double tol2;      // tol^2
+  double tol2b2;    // tol^2 |b|^2
+  double b2;        // |b|^2
+  double rr;        // |r|^2 of the current residual
+  double alpha, beta;
+  double a_re, a_im;  // p = a r + beta p (a = 1 except after a reliable update)
+  double maxr;      // max |r| since the last reliable update
+  double rr_true;   // |b - A x|^2 from the last FP64 recomputation
+  double delta;     // reliable-update threshold (0: only to confirm convergence)
+  int iter;
+  int max_iter;
+  int n_ru;
+  int status;       // SlotStatus
+  int ru_pending;   // FP64 true residual to be recomputed in this iteration
+  int pad;
+};
+
+}  // namespace sq

@@ -1,0 +1,127 @@
+// Run-time autotuner of the Dslash launch shape: threads per block and the
+// number of right-hand sides each thread applies a loaded link to.  The
+// paper's QUDA path picks launch parameters "dynamically and automatically"
+// (Sec. 3); this tuner times every candidate with CUDA events on the first
+// use of a (lattice, precision, link format, batch size) key and caches the
+// winner for the context.  SQ_TUNE_CACHE=<file> persists the cache across
+// processes.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "sq_host.h"
+
+namespace sq {
+
+struct Tuner {
+  std::mutex mu;
+  std::map<std::string, DslashConfig> cache;
+  std::string path;
+};
+
+static std::string tune_key(const Geom &g, int prec, int recon, int nrhs) {
+  std::ostringstream s;
+  s << "dslash_v1:" << g.L[0] << "x" << g.L[1] << "x" << g.L[2] << "x" << g.L[3] << ":p" << prec
+    << ":r" << recon << ":n" << nrhs;
+  return s.str();
+}
+
+Tuner *tuner_create() {
+  Tuner *t = new Tuner();
+  const char *p = std::getenv("SQ_TUNE_CACHE");
+  if (p && *p) {
+    t->path = p;
+    std::ifstream in(t->path);
+    std::string key;
+    DslashConfig c;
+    while (in >> key >> c.block >> c.nr) t->cache[key] = c;
+  }
+  return t;
+}
+
+void tuner_destroy(Tuner *t) { delete t; }
+
+static void tuner_save(Tuner *t) {
+  if (t->path.empty()) return;
+  std::ofstream out(t->path);
+  for (auto &kv : t->cache) out << kv.first << " " << kv.second.block << " " << kv.second.nr << "\n";
+}
+
+DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon, int nrhs,
+                          int mode, cudaStream_t st) {
+  (void)mode;  // epilogues add little traffic: one shape per (lattice, prec, recon, nrhs)
+  DslashConfig def;
+  def.block = 256;
+  def.nr = nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1;
+  Tuner *t = ctx->tuner;
+  if (!t || !gf.has(prec, recon)) return def;
+  const std::string key = tune_key(gf.g, prec, recon, nrhs);
+  std::lock_guard<std::mutex> lk(t->mu);
+  auto it = t->cache.find(key);
+  if (it != t->cache.end()) return it->second;
+  cudaStreamCaptureStatus cs;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return def;
+
+  const Geom &g = gf.g;
+  size_t fb = spinor_bytes(prec, g.stride);
+  void *in = nullptr, *out = nullptr;
+  if (cudaMalloc(&in, fb * nrhs) != cudaSuccess) return def;
+  if (cudaMalloc(&out, fb * nrhs) != cudaSuccess) {
+    cudaFree(in);
+    return def;
+  }
+  cudaMemsetAsync(in, 0, fb * nrhs, st);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  DslashArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = g;
+  a.out_parity = 1;
+  a.links = gf.link_ptr(prec, recon, 1);
+  a.ls = gf.scales(prec, recon);
+  a.in = static_cast<const char *>(in);
+  a.out = static_cast<char *>(out);
+  a.in_fb = a.out_fb = fb;
+  a.nrhs = nrhs;
+  a.gate = GATE_NONE;
+  std::vector<int> nrs = {1};
+  if (nrhs >= 2) nrs.push_back(2);
+  if (nrhs >= 4) nrs.push_back(4);
+  float best = 1e30f;
+  DslashConfig best_c = def;
+  const int reps = 5;
+  for (int nr : nrs) {
+    for (int block = 128; block <= 512; block += 128) {
+      if (launch_dslash(prec, recon, nr, MODE_PLAIN, prec, a, block, st) != 0) continue;
+      cudaEventRecord(e0, st);
+      for (int k = 0; k < reps; ++k) launch_dslash(prec, recon, nr, MODE_PLAIN, prec, a, block, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ctx->launches += reps + 1;
+      if (cudaGetLastError() == cudaSuccess && ms < best) {
+        best = ms;
+        best_c.block = block;
+        best_c.nr = nr;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(in);
+  cudaFree(out);
+  t->cache[key] = best_c;
+  tuner_save(t);
+  return best_c;
+}
+
+}  // namespace sq

@@ -1,0 +1,358 @@
+"""Python binding of libsq.so (the C ABI in include/sq.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA
+library.  There is no CPU fallback -- importing this module without a built
+libsq.so raises, and every call that fails returns its status as an
+``SqError``.  Device buffers are torch CUDA tensors (PyTorch supplies device
+memory and streams); host buffers are numpy arrays.
+
+Method names follow the C entry points: ``gauge_load``, ``dslash_apply``,
+``mdagm_apply``, ``cg_solve``, ``cg_solve_multi``, ``cg_solve_multishift``,
+``serve_submit``, ``serve_poll`` ...; module-level functions of the same
+names take the context as first argument.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, 'libsq.so')
+
+OK, PENDING, NOT_CONVERGED = 0, 1, 2
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE = -1, -2, -3, -4
+ERR_TIMEOUT, ERR_BUSY, ERR_NOTFOUND, ERR_UNSUPPORTED = -5, -6, -7, -8
+PREC = {'f64': 0, 'f32': 1, 'i16': 2}
+
+GAUGE_DEVICE_PTRS = 0x1
+GAUGE_ANTIPERIODIC_T = 0x2
+GAUGE_NO_F32 = 0x10
+GAUGE_NO_I16 = 0x20
+GAUGE_NO_LONG12 = 0x40
+CG_DEVICE_PTRS = 0x1
+CG_INITIAL_GUESS = 0x2
+CG_NO_GRAPH = 0x4
+
+
+class SqError(RuntimeError):
+    def __init__(self, status, what=''):
+        self.status = status
+        super().__init__('%s: %s (status %d)' % (what, _strerror(status), status))
+
+
+class CgOpts(ctypes.Structure):
+    _fields_ = [('precision', ctypes.c_int), ('long_recon', ctypes.c_int),
+                ('delta', ctypes.c_double), ('max_iter', ctypes.c_int),
+                ('block_iters', ctypes.c_int), ('flags', ctypes.c_uint),
+                ('stream', ctypes.c_void_p)]
+
+
+class CgStats(ctypes.Structure):
+    _fields_ = [('status', ctypes.c_int), ('iterations', ctypes.c_int),
+                ('reliable_updates', ctypes.c_int), ('true_residual', ctypes.c_double),
+                ('seconds', ctypes.c_double), ('gflops', ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [('submitted', ctypes.c_uint64), ('completed', ctypes.c_uint64),
+                ('rejected', ctypes.c_uint64), ('queued', ctypes.c_int),
+                ('running', ctypes.c_int), ('p50_ms', ctypes.c_double),
+                ('p99_ms', ctypes.c_double), ('mean_ms', ctypes.c_double),
+                ('solves_per_s', ctypes.c_double), ('hbm_in_use', ctypes.c_size_t),
+                ('hbm_budget', ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# symbol -> (restype, argtypes)
+_P, _I, _U, _D, _SZ, _U64 = (ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_double,
+                             ctypes.c_size_t, ctypes.c_uint64)
+SIGNATURES = {
+    'sq_create': (_I, [ctypes.POINTER(_P), _I, _SZ]),
+    'sq_destroy': (_I, [_P]),
+    'sq_strerror': (ctypes.c_char_p, [_I]),
+    'sq_cg_opts_default': (None, [ctypes.POINTER(CgOpts)]),
+    'sq_kernel_launches': (_U64, [_P]),
+    'gauge_load': (_I, [_P, _P, _P, _P, _U, ctypes.POINTER(_I)]),
+    'gauge_free': (_I, [_P, _I]),
+    'sq_spinor_bytes': (_I, [_P, _I, _I, ctypes.POINTER(_SZ), ctypes.POINTER(_I)]),
+    'sq_pack_spinor': (_I, [_P, _I, _I, _P, _P, _P]),
+    'sq_unpack_spinor': (_I, [_P, _I, _I, _P, _P, _P]),
+    'dslash_apply': (_I, [_P, _I, _I, _I, _I, _P, _P, _P]),
+    'mdagm_apply': (_I, [_P, _I, _I, _I, _D, _P, _P, _P]),
+    'cg_solve': (_I, [_P, _I, _P, _D, _D, ctypes.POINTER(CgOpts), _P, ctypes.POINTER(CgStats)]),
+    'cg_solve_multi': (_I, [_P, _I, _I, _P, _P, _D, ctypes.POINTER(CgOpts), _P,
+                            ctypes.POINTER(CgStats)]),
+    'cg_solve_multishift': (_I, [_P, _I, _P, _I, _P, _D, ctypes.POINTER(CgOpts), _P,
+                                 ctypes.POINTER(CgStats)]),
+    'serve_submit': (_I, [_P, _I, _P, _D, _D, ctypes.POINTER(_U64)]),
+    'serve_poll': (_I, [_P, _U64, _P, ctypes.POINTER(CgStats), _I]),
+    'serve_cancel': (_I, [_P, _U64]),
+    'serve_stats': (_I, [_P, ctypes.POINTER(ServeStats), _I]),
+    'serve_configure': (_I, [_P, _I, _I]),
+}
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libsq.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError('libsq.so not built at %s: run `python -c "import __graft_entry__ '
+                              'as g; g.build()"`' % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _strerror(status):
+    try:
+        return load_library().sq_strerror(status).decode()
+    except Exception:  # noqa: BLE001 - message only
+        return 'status %d' % status
+
+
+def _check(status, what, allow=(OK,)):
+    if status not in allow:
+        raise SqError(status, what)
+    return status
+
+
+def _ptr(x):
+    """Address of a numpy array or torch tensor (or an int address)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags['C_CONTIGUOUS']:
+            raise ValueError('array must be C-contiguous')
+        return x.ctypes.data
+    if hasattr(x, 'data_ptr'):
+        if not x.is_contiguous():
+            raise ValueError('tensor must be contiguous')
+        return x.data_ptr()
+    raise TypeError('expected numpy array, torch tensor or address')
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def _is_device(x):
+    return hasattr(x, 'is_cuda') and x.is_cuda
+
+
+class Context:
+    """A library context on one CUDA device (owns gauge fields and workspaces)."""
+
+    def __init__(self, device=0, hbm_budget=0):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self._lib.sq_create(ctypes.byref(h), int(device), int(hbm_budget)), 'sq_create')
+        self.handle = h
+        self.device = device
+        self._dims = {}
+
+    def close(self):
+        if self.handle:
+            self._lib.sq_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def kernel_launches(self):
+        return int(self._lib.sq_kernel_launches(self.handle))
+
+    # ---------------------------------------------------------------- gauge
+    def gauge_load(self, dims, fat, lng, antiperiodic_t=False, flags=0):
+        dims_a = (ctypes.c_int * 4)(*[int(d) for d in dims])
+        if _is_device(fat):
+            flags |= GAUGE_DEVICE_PTRS
+        else:
+            fat = np.ascontiguousarray(fat, dtype=np.complex128)
+            lng = np.ascontiguousarray(lng, dtype=np.complex128)
+        if antiperiodic_t:
+            flags |= GAUGE_ANTIPERIODIC_T
+        gid = ctypes.c_int(0)
+        _check(self._lib.gauge_load(self.handle, dims_a, _ptr(fat), _ptr(lng), flags,
+                                    ctypes.byref(gid)), 'gauge_load')
+        self._dims[gid.value] = tuple(int(d) for d in dims)
+        return gid.value
+
+    def gauge_free(self, gauge_id):
+        _check(self._lib.gauge_free(self.handle, gauge_id), 'gauge_free')
+        self._dims.pop(gauge_id, None)
+
+    def vh(self, gauge_id):
+        return int(np.prod(self._dims[gauge_id])) // 2
+
+    def spinor_bytes(self, gauge_id, prec):
+        b, s = ctypes.c_size_t(0), ctypes.c_int(0)
+        _check(self._lib.sq_spinor_bytes(self.handle, gauge_id, PREC[prec], ctypes.byref(b),
+                                         ctypes.byref(s)), 'sq_spinor_bytes')
+        return b.value, s.value
+
+    def pack_spinor(self, gauge_id, prec, canon_dev, packed_dev, stream=None):
+        _check(self._lib.sq_pack_spinor(self.handle, gauge_id, PREC[prec], _ptr(canon_dev),
+                                        _ptr(packed_dev), _stream(stream)), 'sq_pack_spinor')
+
+    def unpack_spinor(self, gauge_id, prec, packed_dev, canon_dev, stream=None):
+        _check(self._lib.sq_unpack_spinor(self.handle, gauge_id, PREC[prec], _ptr(packed_dev),
+                                          _ptr(canon_dev), _stream(stream)), 'sq_unpack_spinor')
+
+    # ------------------------------------------------------------ operators
+    def dslash_apply(self, gauge_id, out_parity, prec, long_recon, in_dev, out_dev, stream=None):
+        _check(self._lib.dslash_apply(self.handle, gauge_id, int(out_parity), PREC[prec],
+                                      int(long_recon), _ptr(in_dev), _ptr(out_dev),
+                                      _stream(stream)), 'dslash_apply')
+
+    def mdagm_apply(self, gauge_id, prec, long_recon, mass, in_dev, out_dev, stream=None):
+        _check(self._lib.mdagm_apply(self.handle, gauge_id, PREC[prec], int(long_recon),
+                                     float(mass), _ptr(in_dev), _ptr(out_dev), _stream(stream)),
+               'mdagm_apply')
+
+    # --------------------------------------------------------------- solvers
+    def _opts(self, precision, long_recon, delta, max_iter, block_iters, flags, stream):
+        o = CgOpts()
+        self._lib.sq_cg_opts_default(ctypes.byref(o))
+        o.precision = PREC[precision]
+        o.long_recon = int(long_recon)
+        o.delta = float(delta)
+        o.max_iter = int(max_iter)
+        o.block_iters = int(block_iters)
+        o.flags = flags
+        o.stream = _stream(stream)
+        return o
+
+    def cg_solve(self, gauge_id, src, mass, tol, precision='f32', long_recon=18, delta=0.1,
+                 max_iter=100000, block_iters=16, x0=None, graph=True, stream=None,
+                 check=True, out=None):
+        """Solve (m^2 - D_eo D_oe) x = src.  Returns (x, stats dict).
+
+        src: numpy (Vh, 3) complex128 (host) or a torch complex128 CUDA tensor
+        (device; x is then a device tensor).
+        """
+        xs, st, status = self.cg_solve_multi(gauge_id, [src] if not _is_device(src) else src[None],
+                                             [mass], tol, precision, long_recon, delta, max_iter,
+                                             block_iters, None if x0 is None else
+                                             ([x0] if not _is_device(x0) else x0[None]),
+                                             graph, stream, check, out=out)
+        return xs[0], st[0]
+
+    def cg_solve_multi(self, gauge_id, srcs, masses, tol, precision='f32', long_recon=18,
+                       delta=0.1, max_iter=100000, block_iters=16, x0=None, graph=True,
+                       stream=None, check=True, out=None):
+        """Batched solve; returns (x (nrhs, Vh, 3), [stats dicts], status)."""
+        dev = _is_device(srcs)
+        if dev:
+            import torch
+            src = srcs.contiguous()
+            nrhs = src.shape[0]
+            if out is not None:
+                x = out
+            elif x0 is not None:
+                x = x0.clone().contiguous()
+            else:
+                x = torch.empty_like(src)
+        else:
+            src = np.ascontiguousarray(np.stack([np.asarray(s) for s in srcs]),
+                                       dtype=np.complex128)
+            nrhs = src.shape[0]
+            x = (np.ascontiguousarray(np.stack(list(x0)), dtype=np.complex128) if x0 is not None
+                 else np.zeros_like(src))
+        flags = (CG_DEVICE_PTRS if dev else 0) | (CG_INITIAL_GUESS if x0 is not None else 0)
+        if not graph:
+            flags |= CG_NO_GRAPH
+        o = self._opts(precision, long_recon, delta, max_iter, block_iters, flags, stream)
+        m = np.ascontiguousarray(masses, dtype=np.float64)
+        stats = (CgStats * nrhs)()
+        status = self._lib.cg_solve_multi(self.handle, gauge_id, nrhs, _ptr(src), _ptr(m),
+                                          float(tol), ctypes.byref(o), _ptr(x), stats)
+        if check:
+            _check(status, 'cg_solve', allow=(OK,))
+        return x, [s.as_dict() for s in stats], status
+
+    def cg_solve_multishift(self, gauge_id, src, masses, tol, precision='f32', long_recon=18,
+                            delta=0.1, max_iter=100000, block_iters=16, stream=None, check=True):
+        """Multi-shift solve; returns (x (nshift, Vh, 3), [stats dicts], status)."""
+        dev = _is_device(src)
+        ns = len(masses)
+        if dev:
+            import torch
+            s = src.contiguous()
+            x = torch.empty((ns,) + tuple(s.shape), dtype=s.dtype, device=s.device)
+        else:
+            s = np.ascontiguousarray(src, dtype=np.complex128)
+            x = np.zeros((ns,) + s.shape, dtype=np.complex128)
+        o = self._opts(precision, long_recon, delta, max_iter, block_iters,
+                       CG_DEVICE_PTRS if dev else 0, stream)
+        m = np.ascontiguousarray(masses, dtype=np.float64)
+        stats = (CgStats * ns)()
+        status = self._lib.cg_solve_multishift(self.handle, gauge_id, _ptr(s), ns, _ptr(m),
+                                               float(tol), ctypes.byref(o), _ptr(x), stats)
+        if check:
+            _check(status, 'cg_solve_multishift')
+        return x, [st.as_dict() for st in stats], status
+
+    # --------------------------------------------------------------- serving
+    def serve_configure(self, slots_per_batch=8, block_iters=8):
+        _check(self._lib.serve_configure(self.handle, int(slots_per_batch), int(block_iters)),
+               'serve_configure')
+
+    def serve_submit(self, gauge_id, src, mass, tol):
+        src = np.ascontiguousarray(src, dtype=np.complex128)
+        t = ctypes.c_uint64(0)
+        _check(self._lib.serve_submit(self.handle, gauge_id, _ptr(src), float(mass), float(tol),
+                                      ctypes.byref(t)), 'serve_submit')
+        return t.value
+
+    def serve_poll(self, ticket, vh=None, timeout_us=-1, want_x=True):
+        """Returns (status, x or None, stats dict)."""
+        x = np.zeros((vh, 3), dtype=np.complex128) if (want_x and vh) else None
+        st = CgStats()
+        status = self._lib.serve_poll(self.handle, ctypes.c_uint64(ticket), _ptr(x),
+                                      ctypes.byref(st), int(timeout_us))
+        return status, x, st.as_dict()
+
+    def serve_cancel(self, ticket):
+        return self._lib.serve_cancel(self.handle, ctypes.c_uint64(ticket))
+
+    def serve_stats(self, reset=False):
+        st = ServeStats()
+        _check(self._lib.serve_stats(self.handle, ctypes.byref(st), int(bool(reset))),
+               'serve_stats')
+        return st.as_dict()
+
+
+def _forward(name):
+    def f(ctx, *args, **kw):
+        return getattr(ctx, name)(*args, **kw)
+    f.__name__ = name
+    f.__doc__ = 'Module-level form of Context.%s(ctx, ...).' % name
+    return f
+
+
+for _n in ('gauge_load', 'gauge_free', 'dslash_apply', 'mdagm_apply', 'cg_solve',
+           'cg_solve_multi', 'cg_solve_multishift', 'serve_submit', 'serve_poll',
+           'serve_cancel', 'serve_stats', 'serve_configure'):
+    globals()[_n] = _forward(_n)

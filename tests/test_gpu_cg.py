@@ -1,0 +1,182 @@
+"""GPU CG solves vs the FP64 oracle.
+
+A solve passes when (i) the oracle's own FP64 true residual |b - A x|/|b| of
+the GPU solution is <= tol, (ii) |A (x - x_ref)|/|b| <= 10 tol against the
+oracle's solution x_ref, and (iii) |x - x_ref| <= (|r| + |r_ref|)/m^2
+(A >= m^2).  Where the oracle cannot solve at full size in seconds, (i) alone
+is checked -- it holds at any size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import gauge, o9_check
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve_ref(dims, fat, lng, mass, b, tol=1e-12):
+    x, it, tr = oracle.cg(dims, fat, lng, mass, b, tol, max_iter=20000)
+    assert it > 0 and tr <= tol
+    return x
+
+
+def test_config1_fp64_4444(sq):
+    """4^4, eps 0.3, am 0.05, tol 1e-10, FP64 everywhere."""
+    dims = (4, 4, 4, 4)
+    fat, lng = gauge(dims, 0.3, 0)
+    b = synth.gaussian_source(128, 0)
+    gid = sq.gauge_load(dims, fat, lng)
+    try:
+        x, st = sq.cg_solve(gid, b, 0.05, 1e-10, precision='f64')
+        assert st['status'] == 0 and st['true_residual'] <= 1e-10
+        x_ref = _solve_ref(dims, fat, lng, 0.05, b)
+        o9_check(dims, fat, lng, 0.05, b, x, x_ref, 1e-10)
+        _, it_o, _ = oracle.cg(dims, fat, lng, 0.05, b, 1e-10)
+        assert abs(st['iterations'] - it_o) <= 3
+    finally:
+        sq.gauge_free(gid)
+
+
+@pytest.mark.parametrize('prec,recon', [('f32', 18), ('f32', 12), ('i16', 18), ('i16', 12),
+                                        ('f64', 12)])
+@pytest.mark.parametrize('dims', [(8, 8, 8, 8), (4, 6, 8, 10)])
+def test_mixed_precision_solves(sq, prec, recon, dims):
+    fat, lng = gauge(dims, 0.25, 0)
+    vh = oracle.volume(dims) // 2
+    b = synth.gaussian_source(vh, 0)
+    mass, tol = 0.05, 1e-8
+    gid = sq.gauge_load(dims, fat, lng)
+    try:
+        x, st = sq.cg_solve(gid, b, mass, tol, precision=prec, long_recon=recon)
+        assert st['status'] == 0
+        if prec != 'f64':
+            assert st['reliable_updates'] >= 2
+        x_ref = _solve_ref(dims, fat, lng, mass, b)
+        r, err = o9_check(dims, fat, lng, mass, b, x, x_ref, tol)
+        assert abs(r - st['true_residual']) <= 1e-3 * tol + 1e-6 * r
+    finally:
+        sq.gauge_free(gid)
+
+
+def test_free_field_solution_closed_form(sq):
+    """Unit links, plane-wave source: x = b / (m^2 + S(p)) exactly."""
+    dims = (8, 4, 4, 8)
+    vol = oracle.volume(dims)
+    u = np.broadcast_to(np.eye(3, dtype=np.complex128), (vol, 4, 3, 3)).copy()
+    fat, lng = synth.fat_long_links(u, dims)
+    lex = oracle.half_sites(dims, 0)
+    lx, ly, lz, lt = dims
+    c = np.stack([lex % lx, (lex // lx) % ly, (lex // (lx * ly)) % lz, lex // (lx * ly * lz)], 1)
+    b = np.zeros((vol // 2, 3), dtype=np.complex128)
+    x_exact = np.zeros_like(b)
+    mass = 0.02
+    for n, col in [((1, 0, 0, 1), [1, 0, 0]), ((0, 1, 1, 3), [0, 1j, 0.5]), ((2, 1, 0, 2), [0.3, 0, -1])]:
+        p = 2 * np.pi * np.array(n) / np.array(dims)
+        pw = np.exp(1j * c @ p)[:, None] * np.array(col)[None, :]
+        s = sum((synth.C1 * np.sin(q) + synth.C3 * np.sin(3 * q)) ** 2 for q in p)
+        b += pw
+        x_exact += pw / (mass ** 2 + s)
+    gid = sq.gauge_load(dims, fat, lng)
+    try:
+        for prec in ('f64', 'f32'):
+            x, st = sq.cg_solve(gid, b, mass, 1e-10, precision=prec)
+            assert st['status'] == 0
+            assert np.linalg.norm(x - x_exact) <= 1e-10 / mass ** 2 * np.linalg.norm(b) * 2
+    finally:
+        sq.gauge_free(gid)
+
+
+def test_initial_guess_and_zero_source(sq):
+    dims = (4, 4, 4, 8)
+    fat, lng = gauge(dims, 0.3, 0)
+    vh = oracle.volume(dims) // 2
+    b = synth.gaussian_source(vh, 2)
+    gid = sq.gauge_load(dims, fat, lng)
+    try:
+        x1, st1 = sq.cg_solve(gid, b, 0.05, 1e-6, precision='f32')
+        x2, st2 = sq.cg_solve(gid, b, 0.05, 1e-10, precision='f32', x0=x1)
+        assert st2['status'] == 0 and st2['iterations'] < st1['iterations'] + 200
+        assert oracle.true_residual(dims, fat, lng, 0.05, b, x2) <= 1e-10
+        # exact solution as guess: converged without iterating
+        x3, st3 = sq.cg_solve(gid, b, 0.05, 1e-6, precision='f32', x0=x2)
+        assert st3['status'] == 0 and st3['iterations'] == 0
+        z, stz = sq.cg_solve(gid, np.zeros_like(b), 0.05, 1e-10)
+        assert stz['status'] == 0 and stz['iterations'] == 0 and np.all(z == 0)
+    finally:
+        sq.gauge_free(gid)
+
+
+def test_error_paths(sq):
+    from paper_1411_2223_gb300 import sq as sqm
+    dims = (4, 4, 4, 4)
+    fat, lng = gauge(dims, 0.3, 0)
+    b = synth.gaussian_source(128, 0)
+    gid = sq.gauge_load(dims, fat, lng)
+    try:
+        bad = b.copy()
+        bad[3, 1] = np.inf
+        with pytest.raises(sqm.SqError) as e:
+            sq.cg_solve(gid, bad, 0.05, 1e-8)
+        assert e.value.status == sqm.ERR_NONFINITE
+        for mass, tol in [(0.0, 1e-8), (-1.0, 1e-8), (0.05, 0.0), (0.05, np.nan)]:
+            with pytest.raises(sqm.SqError) as e:
+                sq.cg_solve(gid, b, mass, tol)
+            assert e.value.status == sqm.ERR_ARG
+        with pytest.raises(sqm.SqError) as e:
+            sq.cg_solve(gid + 100, b, 0.05, 1e-8)
+        assert e.value.status == sqm.ERR_NOTFOUND
+        x, st = sq.cg_solve(gid, b, 0.05, 1e-12, max_iter=5, check=False)
+        assert st['status'] == sqm.NOT_CONVERGED and st['iterations'] == 5
+        assert 0 < st['true_residual'] < 1
+    finally:
+        sq.gauge_free(gid)
+
+
+def test_graph_and_direct_launches_agree_bitwise(sq):
+    dims = (8, 4, 4, 8)
+    fat, lng = gauge(dims, 0.25, 0)
+    b = synth.gaussian_source(oracle.volume(dims) // 2, 4)
+    gid = sq.gauge_load(dims, fat, lng)
+    try:
+        xa, sa = sq.cg_solve(gid, b, 0.05, 1e-9, graph=True)
+        xb, sb = sq.cg_solve(gid, b, 0.05, 1e-9, graph=False)
+        xc, sc = sq.cg_solve(gid, b, 0.05, 1e-9, graph=True, block_iters=5)
+        assert np.array_equal(xa, xb) and np.array_equal(xa, xc)
+        assert sa['iterations'] == sb['iterations'] == sc['iterations']
+    finally:
+        sq.gauge_free(gid)
+
+
+def test_device_pointer_solve(sq):
+    import torch
+    dims = (8, 8, 4, 8)
+    fat, lng = gauge(dims, 0.25, 0)
+    vh = oracle.volume(dims) // 2
+    b = synth.gaussian_source(vh, 6)
+    gid = sq.gauge_load(dims, torch.from_numpy(fat).cuda(), torch.from_numpy(lng).cuda())
+    try:
+        xd, st = sq.cg_solve(gid, torch.from_numpy(b).cuda(), 0.05, 1e-8)
+        xh, sth = sq.cg_solve(gid, b, 0.05, 1e-8)
+        assert np.array_equal(xd.cpu().numpy(), xh)
+        assert oracle.true_residual(dims, fat, lng, 0.05, b, xh) <= 1e-8
+    finally:
+        sq.gauge_free(gid)
+
+
+@pytest.mark.parametrize('prec,recon', [('f32', 18), ('f32', 12), ('i16', 12), ('f64', 18)])
+def test_config2_full_size_20x64(sq, prec, recon):
+    """20^3 x 64, eps 0.25, am 0.01, tol 1e-8 (the benchmark workload)."""
+    dims = (20, 20, 20, 64)
+    fat, lng = gauge(dims, 0.25, 0)
+    vh = oracle.volume(dims) // 2
+    b = synth.gaussian_source(vh, 0)
+    gid = sq.gauge_load(dims, fat, lng)
+    try:
+        x, st = sq.cg_solve(gid, b, 0.01, 1e-8, precision=prec, long_recon=recon)
+        assert st['status'] == 0
+        r = oracle.true_residual(dims, fat, lng, 0.01, b, x)
+        assert r <= 1e-8, r
+    finally:
+        sq.gauge_free(gid)
