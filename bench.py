@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Benchmark of the asqtad mixed-precision CG on one GB300 (or N replicas).
+
+Workload (the paper's lattice shape, Sec. 2 / Fig. 1): a 20^3 x 64 synthetic
+near-identity gauge field (thin links exp(i 0.25 H), seed 0, fat/long input
+recipe), Gaussian source (seed 0), am = 0.01, relative residual 1e-8.
+
+One step = one solve of (m^2 - D_eo D_oe) x = b to 1e-8: FP32 inner CG with
+FP64 reliable updates and FP64 solution accumulation, source and solution
+resident on the device.  The JSON line also carries the plain FP64 GPU CG on
+the same problem (same kernel template), the Dslash throughput per storage
+format, the 16-bit mixed solve, the HBM roofline of the dominant kernel, the
+end-to-end time through the C ABI with host buffers, the CPU oracle baseline
+and the SM clocks seen during the timed region.
+
+``--impl reference`` times the CPU oracle instead (the reference arm).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = 'CG time-to-1e-8 & Dslash GB/s at 20^3x64 vs FP64 CG; serve p50/p99 latency'
+DIMS = (20, 20, 20, 64)
+EPS, GAUGE_SEED, SRC_SEED, MASS, TOL = 0.25, 0, 0, 0.01, 1e-8
+# Algorithmic bytes per output site of one Dslash: 16 links + 1 input + 1 output
+# colour vector (neighbour gathers hit L2).
+DSLASH_BYTES = {('f64', 18): 2400, ('f64', 12): 2016, ('f32', 18): 1200, ('f32', 12): 1008,
+                ('i16', 18): 608, ('i16', 12): 512}
+DSLASH_FLOPS = 1146
+CG_FLOPS_PER_SITE_ITER = 2364
+PAPER_CONTEXT_GFLOPS = 46.48   # mixed-precision CG, GTX Titan Black (Table 2)
+# DRAM traffic of one FP32 18-real Dslash launch at 20^3 x 64 from an ncu
+# capture of the kernel source with this fingerprint (None: not captured).
+NCU_TRAFFIC = {'fingerprint': None, 'bytes_per_launch': None}
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument('--gpus', type=int, default=1)
+    p.add_argument('--steps', type=int, default=5)
+    p.add_argument('--warmup', type=int, default=3)
+    p.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    p.add_argument('--cpu-sample-s', type=float, default=15.0,
+                   help='seconds of oracle work in the CPU baseline sample')
+    p.add_argument('--no-cpu-baseline', action='store_true')
+    p.add_argument('--dslash-iters', type=int, default=200)
+    p.add_argument('--dslash-only', default=None, metavar='FORMATS',
+                   help='profiling aid: only time the Dslash in these formats '
+                        '(comma list of prec_recon, e.g. f32_18), no solves')
+    return p.parse_args()
+
+
+def kernel_fingerprint():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, 'paper_1411_2223_gb300', 'csrc')
+    for f in ('dslash.cuh', 'sq_device.cuh', 'dslash_f32.cu'):
+        h.update(open(os.path.join(csrc, f), 'rb').read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, 'MEASURED_PEAKS.json')
+    try:
+        d = json.load(open(path))
+        return float(d['hbm_gbs']), 'measured'
+    except Exception:  # noqa: BLE001
+        return 6800.0, 'fallback'
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+              'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+              'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix='.csv')
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ['nvidia-smi', '-i', str(self.device), '--query-gpu=' + self.FIELDS,
+                 '--format=csv,noheader,nounits', '-lms', '200'],
+                stdout=open(self.path, 'w'), stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(',')]
+                if len(f) >= 9 and f[1].replace('.', '').isdigit():
+                    rows.append(f)
+        except Exception:  # noqa: BLE001
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['unavailable'], 'samples': 0}
+        sm = [float(r[1]) for r in rows]
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == 'Active'})
+        loaded = [s for s, r in zip(sm, rows) if float(r[3] or 0) > 200.0] or sm
+        return {'sm_mhz': statistics.median(loaded), 'sm_max_mhz': float(rows[0][2]),
+                'reasons': reasons, 'samples': len(rows),
+                'power_w_max': max(float(r[3] or 0) for r in rows)}
+
+
+# ------------------------------------------------------------------- CPU oracle
+
+def cpu_baseline(fat, lng, b, sample_s):
+    """Oracle FP64 CG on the host cores: a bounded number of iterations on the
+    full workload, extrapolated to the oracle's own iteration count to 1e-8
+    (stored by tests/golden/make_golden.py, which runs only the oracle)."""
+    import oracle
+    gold = json.load(open(os.path.join(ROOT, 'tests', 'golden', 'oracle_cg.json')))
+    iters_full = gold['cg_20x20x20x64_m0.01_tol1e-8']['iterations']
+    t0 = time.time()
+    oracle.cg(DIMS, fat, lng, MASS, b, TOL, max_iter=2)
+    per_iter = (time.time() - t0) / 3.0          # 2 iterations + final true residual
+    n = max(2, min(200, int(sample_s / max(per_iter, 1e-3))))
+    t0 = time.time()
+    oracle.cg(DIMS, fat, lng, MASS, b, TOL, max_iter=n)
+    el = time.time() - t0
+    per_iter = el / (n + 1)
+    cores = int(os.environ.get('OMP_NUM_THREADS', os.cpu_count() or 1))
+    return {'value': per_iter * iters_full * 1e3, 'unit': 'ms', 'cores': cores, 'kind': 'oracle',
+            'sample': '%d oracle FP64 CG iterations on the 20^3x64 workload (%.1f s), scaled by '
+                      'the oracle\'s %d iterations to 1e-8' % (n, el, iters_full),
+            'ms_per_iteration': per_iter * 1e3}
+
+
+def run_reference(args):
+    rank = int(os.environ.get('RANK', '0'))
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    import synth
+    fat, lng = synth.gauge_field(DIMS, EPS, GAUGE_SEED)
+    b = synth.gaussian_source(int(np.prod(DIMS)) // 2, SRC_SEED)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(fat, lng, b, args.cpu_sample_s / 3)
+        if k >= args.warmup:
+            vals.append(cb['value'])
+    v = statistics.median(vals)
+    line = {'impl': 'reference', 'metric': METRIC, 'value': v, 'unit': 'ms', 'n_gpus': args.gpus,
+            'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': v,
+            'higher_is_better': False, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
+            'data': 'synthetic', 'config': config_dict(),
+            'cpu_baseline': dict(cb, value=v),
+            'e2e': {'value': v, 'unit': 'ms', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict():
+    return {'workload': 'asqtad even-odd CG 20^3x64 (eps 0.25 synthetic links, seed 0), '
+                        'am 0.01, tol 1e-8, 1 RHS, FP32 inner CG + FP64 reliable updates',
+            'lattice': 'x'.join(map(str, DIMS)), 'mass': MASS, 'tol': TOL, 'rhs': 1,
+            'l2': 'inputs larger than L2: FP32 links 295 MB per parity, both parities per '
+                  'iteration; Dslash timing alternates parities',
+            'parallelism': 'replicas'}
+
+
+# ------------------------------------------------------------------- GPU arm
+
+def time_dslash(ctx, gid, b_dev, stream, vh, formats, iters):
+    """Average device time per Dslash launch (CUDA events on the launching
+    stream), alternating output parities so both link fields stream from HBM."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    bufs = {}
+    for prec, recon in formats:
+        nbytes, _ = ctx.spinor_bytes(gid, prec)
+        if prec not in bufs:
+            bufs[prec] = (torch.zeros(nbytes, dtype=torch.uint8, device='cuda'),
+                          torch.zeros(nbytes, dtype=torch.uint8, device='cuda'))
+            ctx.pack_spinor(gid, prec, b_dev, bufs[prec][0], stream)
+            ctx.pack_spinor(gid, prec, b_dev, bufs[prec][1], stream)
+        a, c = bufs[prec]
+        n_it = iters if prec != 'f64' else max(20, iters // 4)
+        for k in range(20):
+            ctx.dslash_apply(gid, k & 1, prec, recon, a if k & 1 else c, c if k & 1 else a, stream)
+        ev0.record(stream)
+        for k in range(n_it):
+            ctx.dslash_apply(gid, k & 1, prec, recon, a if k & 1 else c, c if k & 1 else a, stream)
+        ev1.record(stream)
+        ev1.synchronize()
+        us = ev0.elapsed_time(ev1) * 1e3 / n_it
+        gbs = DSLASH_BYTES[(prec, recon)] * vh / (us * 1e-6) / 1e9
+        out['%s_%d' % (prec, recon)] = {'us': round(us, 2), 'GBs': round(gbs, 1),
+                                        'gflops': round(DSLASH_FLOPS * vh / (us * 1e-6) / 1e9, 1)}
+    return out
+
+
+def main():
+    args = parse_args()
+    if args.impl == 'reference':
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1411_2223_gb300 import sq
+
+    world = int(os.environ.get('WORLD_SIZE', '1'))
+    rank = int(os.environ.get('RANK', '0'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl' if torch.cuda.is_available() else 'gloo')
+    torch.cuda.set_device(local)
+    vh = int(np.prod(DIMS)) // 2
+
+    fat, lng = synth.gauge_field(DIMS, EPS, GAUGE_SEED)
+    b_host = synth.gaussian_source(vh, SRC_SEED)
+    ctx = sq.Context(local)
+    gflags = 0
+    if args.dslash_only:  # load only the link forms being timed
+        want = set(args.dslash_only.split(','))
+        if not any(f.startswith('f64') for f in want):
+            gflags |= sq.GAUGE_NO_F64
+        if not any(f.startswith('f32') for f in want):
+            gflags |= sq.GAUGE_NO_F32
+        if not any(f.startswith('i16') for f in want):
+            gflags |= sq.GAUGE_NO_I16
+        if not any(f.endswith('_12') for f in want):
+            gflags |= sq.GAUGE_NO_LONG12
+    gid = ctx.gauge_load(DIMS, fat, lng, flags=gflags)
+    stream = torch.cuda.Stream()
+    b_dev = torch.from_numpy(b_host).cuda()
+    x_dev = torch.empty_like(b_dev)
+    if args.dslash_only:
+        fmts = [(f.split('_')[0], int(f.split('_')[1])) for f in args.dslash_only.split(',')]
+        res = time_dslash(ctx, gid, b_dev, stream, vh, fmts, args.dslash_iters)
+        print(json.dumps({'dslash': res}))
+        ctx.close()
+        return 0
+
+    def solve(prec='f32', recon=18, dev=True, out=None):
+        if dev:
+            return ctx.cg_solve(gid, b_dev, MASS, TOL, precision=prec, long_recon=recon,
+                                stream=stream, out=x_dev)
+        return ctx.cg_solve(gid, b_host_pinned, MASS, TOL, precision=prec, long_recon=recon,
+                            stream=stream, out=x_host_pinned)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up: tuning, graph capture, first-touch
+    for _ in range(args.warmup):
+        _, st = solve()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    # ---- timed region: K mixed-precision solves, device-resident inputs
+    barrier()
+    l0 = ctx.kernel_launches()
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, st = solve()
+        ev1.record(stream)
+        ev1.synchronize()
+    launches = ctx.kernel_launches() - l0
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device='cuda')
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    iters = st['iterations']
+    clk = clocks.summary()
+
+    # ---- plain FP64 GPU CG on the same problem (same kernel template)
+    k64 = max(1, min(3, args.steps))
+    solve('f64')
+    barrier()
+    ev0.record(stream)
+    for _ in range(k64):
+        _, st64 = solve('f64')
+    ev1.record(stream)
+    ev1.synchronize()
+    ms64 = ev0.elapsed_time(ev1) / k64
+    x64 = x_dev.clone()
+
+    # ---- 16-bit storage mixed solve (12-real long links)
+    solve('i16', 12)
+    ev0.record(stream)
+    for _ in range(k64):
+        _, st16 = solve('i16', 12)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms16 = ev0.elapsed_time(ev1) / k64
+
+    # FP64 error of the mixed result against the FP64 CG solution
+    solve('f32')
+    err = float(torch.linalg.vector_norm(x_dev - x64) / torch.linalg.vector_norm(x64))
+
+    # ---- e2e through the C ABI with host buffers (pinned), copies inside
+    b_host_pinned = torch.from_numpy(b_host).pin_memory().numpy()
+    x_host_pinned = torch.zeros(b_host.shape, dtype=torch.complex128).pin_memory().numpy()
+    solve(dev=False)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        solve(dev=False)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms_e2e = ev0.elapsed_time(ev1) / args.steps
+    h2d = b_host.nbytes
+    d2h = b_host.nbytes
+
+    # ---- Dslash throughput per format (alternating parities: > L2 of links)
+    dslash = time_dslash(ctx, gid, b_dev, stream, vh,
+                         (('f32', 18), ('f32', 12), ('i16', 12), ('i16', 18), ('f64', 18)),
+                         args.dslash_iters)
+    peak, peak_kind = measured_peak()
+    dom = dslash['f32_18']
+    traffic = None
+    if NCU_TRAFFIC['fingerprint'] == kernel_fingerprint():
+        traffic = NCU_TRAFFIC['bytes_per_launch']
+    roofline = {'bound': 'hbm', 'achieved': dom['GBs'], 'peak': peak, 'unit': 'GB/s',
+                'frac': round(dom['GBs'] / peak, 4), 'traffic': traffic,
+                'kernel': 'dslash_kernel<F32,18-real,1 RHS> (D_oe), %d algorithmic B/site x %d '
+                          'sites per launch' % (DSLASH_BYTES[('f32', 18)], vh),
+                'peak_kind': peak_kind + ' (MEASURED_PEAKS.json hbm_gbs, burst)'
+                if peak_kind == 'measured' else 'fallback'}
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(fat, lng, b_host, args.cpu_sample_s)
+
+    if rank == 0:
+        gflops = CG_FLOPS_PER_SITE_ITER * vh * iters / (ms * 1e-3) / 1e9
+        line = {
+            'metric': METRIC, 'value': round(ms, 3), 'unit': 'ms', 'n_gpus': world,
+            'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': round(ms, 3),
+            'higher_is_better': False, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32',
+            'data': 'synthetic', 'config': config_dict(),
+            'iterations': iters, 'reliable_updates': st['reliable_updates'],
+            'true_residual': st['true_residual'], 'cg_gflops': round(gflops, 1),
+            'fp64_cg': {'ms': round(ms64, 3), 'iterations': st64['iterations'],
+                        'true_residual': st64['true_residual']},
+            'speedup_vs_fp64': round(ms64 / ms, 3),
+            'fp64_error_vs_fp64_cg': err,
+            'i16_cg': {'ms': round(ms16, 3), 'iterations': st16['iterations'],
+                       'reliable_updates': st16['reliable_updates'],
+                       'true_residual': st16['true_residual'], 'long_recon': 12},
+            'dslash': dslash,
+            'roofline': roofline,
+            'e2e': {'value': round(ms_e2e, 3), 'unit': 'ms', 'h2d_bytes_per_step': h2d,
+                    'd2h_bytes_per_step': d2h},
+            'gpu_launches': launches,
+            'clocks': clk,
+            'cpu_baseline': cb,
+            'paper_context': {'gflops_mixed_cg_titan_black': PAPER_CONTEXT_GFLOPS,
+                              'note': 'Table 2; different hardware and flop convention'},
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == '__main__':
+    sys.exit(main())

@@ -78,6 +78,7 @@ typedef enum { SQ_PREC_F64 = 0, SQ_PREC_F32 = 1, SQ_PREC_I16 = 2 } sq_prec;
 #define SQ_GAUGE_NO_F32         0x10u /* skip the FP32 forms                      */
 #define SQ_GAUGE_NO_I16         0x20u /* skip the 16-bit forms                    */
 #define SQ_GAUGE_NO_LONG12      0x40u /* skip the 12-real long-link forms         */
+#define SQ_GAUGE_NO_F64         0x80u /* skip the FP64 forms (no solves then)     */
 
 /* sq_cg_opts.flags */
 #define SQ_CG_DEVICE_PTRS   0x1u  /* src/x are device pointers (canonical layout) */
@@ -92,7 +93,8 @@ typedef struct {
     int max_iter;      /* default 100000                                              */
     int block_iters;   /* CG iterations per graph launch (default 16)                 */
     unsigned flags;    /* SQ_CG_* */
-    void *stream;      /* cudaStream_t, NULL = context stream                         */
+    void *stream;      /* cudaStream_t the solve runs on (it still returns only when
+                          done); NULL or a default stream: the context's stream     */
 } sq_cg_opts;
 
 typedef struct {

@@ -269,6 +269,7 @@ extern "C" int gauge_load(sq_ctx *ctx, const int dims[4], const double *fat, con
 
   rc = SQ_OK;
   for (int prec = 0; prec < 3 && rc == SQ_OK; ++prec) {
+    if (prec == PREC_F64 && (flags & SQ_GAUGE_NO_F64)) continue;
     if (prec == PREC_F32 && (flags & SQ_GAUGE_NO_F32)) continue;
     if (prec == PREC_I16 && (flags & SQ_GAUGE_NO_I16)) continue;
     for (int recon : {18, 12}) {
@@ -462,8 +463,13 @@ int solve_batch(sq_ctx *ctx, int gauge_id, int nrhs, const double *src, const do
   std::lock_guard<std::mutex> solve_lock(ctx->solve_mu);
   cudaSetDevice(ctx->device);
   auto t0 = std::chrono::steady_clock::now();
+  // Run on the caller's stream unless it is a default stream (those cannot
+  // be captured into a graph); then the context's stream, after the caller's.
   cudaStream_t st = ctx->stream;
-  if (o.stream) SQ_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)o.stream));
+  cudaStream_t user = (cudaStream_t)o.stream;
+  if (user == cudaStreamLegacy || user == cudaStreamPerThread) user = nullptr;
+  if (user) st = user;
+  else if (o.stream) SQ_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)o.stream));
 
   CGWork *w = nullptr;
   SolveCache *cache;

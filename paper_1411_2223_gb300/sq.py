@@ -30,6 +30,7 @@ GAUGE_ANTIPERIODIC_T = 0x2
 GAUGE_NO_F32 = 0x10
 GAUGE_NO_I16 = 0x20
 GAUGE_NO_LONG12 = 0x40
+GAUGE_NO_F64 = 0x80
 CG_DEVICE_PTRS = 0x1
 CG_INITIAL_GUESS = 0x2
 CG_NO_GRAPH = 0x4
@@ -250,41 +251,45 @@ class Context:
         """Solve (m^2 - D_eo D_oe) x = src.  Returns (x, stats dict).
 
         src: numpy (Vh, 3) complex128 (host) or a torch complex128 CUDA tensor
-        (device; x is then a device tensor).
+        (device; x is then a device tensor).  out: optional buffer for x of the
+        same kind (e.g. pinned host memory or a preallocated device tensor).
         """
-        xs, st, status = self.cg_solve_multi(gauge_id, [src] if not _is_device(src) else src[None],
-                                             [mass], tol, precision, long_recon, delta, max_iter,
-                                             block_iters, None if x0 is None else
-                                             ([x0] if not _is_device(x0) else x0[None]),
-                                             graph, stream, check, out=out)
+        xs, st, status = self.cg_solve_multi(
+            gauge_id, src[None], [mass], tol, precision, long_recon, delta, max_iter,
+            block_iters, None if x0 is None else x0[None], graph, stream, check,
+            out=None if out is None else out[None])
         return xs[0], st[0]
 
     def cg_solve_multi(self, gauge_id, srcs, masses, tol, precision='f32', long_recon=18,
                        delta=0.1, max_iter=100000, block_iters=16, x0=None, graph=True,
                        stream=None, check=True, out=None):
-        """Batched solve; returns (x (nrhs, Vh, 3), [stats dicts], status)."""
+        """Batched solve; returns (x (nrhs, Vh, 3), [stats dicts], status).
+
+        srcs: (nrhs, Vh, 3) numpy array / list of arrays, or a torch CUDA tensor.
+        """
         dev = _is_device(srcs)
         if dev:
-            import torch
             src = srcs.contiguous()
-            nrhs = src.shape[0]
-            if out is not None:
-                x = out
-            elif x0 is not None:
-                x = x0.clone().contiguous()
-            else:
-                x = torch.empty_like(src)
+            x = out if out is not None else src.new_zeros(src.shape)
+            if x0 is not None:
+                x.copy_(x0)
         else:
-            src = np.ascontiguousarray(np.stack([np.asarray(s) for s in srcs]),
-                                       dtype=np.complex128)
-            nrhs = src.shape[0]
-            x = (np.ascontiguousarray(np.stack(list(x0)), dtype=np.complex128) if x0 is not None
-                 else np.zeros_like(src))
+            if isinstance(srcs, np.ndarray):
+                src = np.ascontiguousarray(srcs, dtype=np.complex128)
+            else:
+                src = np.ascontiguousarray(np.stack([np.asarray(v) for v in srcs]),
+                                           dtype=np.complex128)
+            x = out if out is not None else np.zeros_like(src)
+            if x0 is not None:
+                x[...] = np.asarray(x0)
+        nrhs = src.shape[0]
         flags = (CG_DEVICE_PTRS if dev else 0) | (CG_INITIAL_GUESS if x0 is not None else 0)
         if not graph:
             flags |= CG_NO_GRAPH
         o = self._opts(precision, long_recon, delta, max_iter, block_iters, flags, stream)
         m = np.ascontiguousarray(masses, dtype=np.float64)
+        if m.shape != (nrhs,):
+            raise ValueError('one mass per right-hand side')
         stats = (CgStats * nrhs)()
         status = self._lib.cg_solve_multi(self.handle, gauge_id, nrhs, _ptr(src), _ptr(m),
                                           float(tol), ctypes.byref(o), _ptr(x), stats)

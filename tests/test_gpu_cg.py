@@ -129,7 +129,9 @@ def test_error_paths(sq):
         assert e.value.status == sqm.ERR_NOTFOUND
         x, st = sq.cg_solve(gid, b, 0.05, 1e-12, max_iter=5, check=False)
         assert st['status'] == sqm.NOT_CONVERGED and st['iterations'] == 5
-        assert 0 < st['true_residual'] < 1
+        # CG's residual is not monotone: only finiteness and agreement with the oracle
+        r = oracle.true_residual(dims, fat, lng, 0.05, b, x)
+        assert np.isfinite(st['true_residual']) and abs(st['true_residual'] - r) <= 1e-9 * r
     finally:
         sq.gauge_free(gid)
 
