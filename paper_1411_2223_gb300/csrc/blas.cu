@@ -18,33 +18,38 @@ __device__ __forceinline__ bool any_running(const SlotState *s, int n) {
   return any;
 }
 
-// x64 += alpha p ; r -= alpha Ap ; partial |r|^2 ; last block: finish_update
+// xs += alpha p ; r -= alpha Ap ; partial |r|^2 ; last block: finish_update
+// and, inside a conditional graph, switch the reliable-update body on or off.
 template <int S>
 __global__ void __launch_bounds__(256) cg_update_kernel(VecArgs a) {
   using R = typename SpinorIO<S>::R;
-  if (!any_running(a.slots, a.nrhs)) return;
+  constexpr int XP = (S == PREC_F64) ? PREC_F64 : PREC_F32;
+  if (!any_running(a.slots, a.nrhs)) {
+    if (a.set_cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+      cudaGraphSetConditional(a.ru_cond, 0u);
+    return;
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   const int St = a.g.stride;
   SlotState *s = a.slots + r;
   double val[1] = {0.0};
   if (i < a.g.vh && running(s)) {
-    const double alpha = s->alpha;
+    const R al = (R)s->alpha;
     Vec3<R> p = SpinorIO<S>::load(a.p + r * a.fb, St, i);
     Vec3<R> ap = SpinorIO<S>::load(a.ap + r * a.fb, St, i);
     Vec3<R> rv = SpinorIO<S>::load(a.r + r * a.fb, St, i);
-    Vec3<double> x = SpinorIO<PREC_F64>::load(a.x64 + r * a.f64_fb, St, i);
-    const R al = (R)alpha;
+    Vec3<R> x = SpinorIO<XP>::load(a.xs + r * a.xs_fb, St, i);
     R n2 = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      x.c[c].x = fma(alpha, (double)p.c[c].x, x.c[c].x);
-      x.c[c].y = fma(alpha, (double)p.c[c].y, x.c[c].y);
+      x.c[c].x = fma(al, p.c[c].x, x.c[c].x);
+      x.c[c].y = fma(al, p.c[c].y, x.c[c].y);
       rv.c[c].x = fma(-al, ap.c[c].x, rv.c[c].x);
       rv.c[c].y = fma(-al, ap.c[c].y, rv.c[c].y);
       n2 = fma(rv.c[c].x, rv.c[c].x, fma(rv.c[c].y, rv.c[c].y, n2));
     }
-    SpinorIO<PREC_F64>::store(a.x64 + r * a.f64_fb, St, i, x);
+    SpinorIO<XP>::store(a.xs + r * a.xs_fb, St, i, x);
     SpinorIO<S>::store(a.r + r * a.fb, St, i, rv);
     val[0] = (double)n2;
   }
@@ -57,8 +62,35 @@ __global__ void __launch_bounds__(256) cg_update_kernel(VecArgs a) {
       double rr = block_sum_fixed(a.partial + (size_t)k * a.g.nchunks, a.g.nchunks, red);
       if (threadIdx.x == 0) finish_update(a.slots + k, rr);
     }
-    if (threadIdx.x == 0) *a.counter = 0;
+    if (threadIdx.x == 0) {
+      *a.counter = 0;
+      if (a.set_cond) {
+        unsigned any = 0;
+        for (int k = 0; k < a.nrhs; ++k) any |= (a.slots[k].ru_pending != 0);
+        cudaGraphSetConditional(a.ru_cond, any);
+      }
+    }
   }
+}
+
+// Reliable update, first step: x64 += xs, xs = 0 for the flagged systems.
+template <int XP>
+__global__ void __launch_bounds__(256) cg_fold_kernel(VecArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (i >= a.g.vh || !a.slots[r].ru_pending) return;
+  const int St = a.g.stride;
+  auto xs = SpinorIO<XP>::load(a.xs + r * a.xs_fb, St, i);
+  Vec3<double> x = SpinorIO<PREC_F64>::load(a.x64 + r * a.f64_fb, St, i);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    x.c[c].x += (double)xs.c[c].x;
+    x.c[c].y += (double)xs.c[c].y;
+  }
+  SpinorIO<PREC_F64>::store(a.x64 + r * a.f64_fb, St, i, x);
+  decltype(xs) z;
+  zero(z);
+  SpinorIO<XP>::store(a.xs + r * a.xs_fb, St, i, z);
 }
 
 // p = a r + beta p (a complex, 1 except right after a reliable update)
@@ -100,6 +132,12 @@ __global__ void __launch_bounds__(256) cg_init_kernel(VecArgs a, int guess) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) n2 = fma(b.c[c].x, b.c[c].x, fma(b.c[c].y, b.c[c].y, n2));
     val[0] = n2;
+    {
+      constexpr int XP = (S == PREC_F64) ? PREC_F64 : PREC_F32;
+      Vec3<typename SpinorIO<XP>::R> z;
+      zero(z);
+      SpinorIO<XP>::store(a.xs + r * a.xs_fb, St, i, z);
+    }
     if (guess) {
       Vec3<R> z;
       zero(z);
@@ -181,6 +219,14 @@ int launch_cg_update(int prec, const VecArgs &a, cudaStream_t st) {
     case PREC_I16: cg_update_kernel<PREC_I16><<<grid, 256, 0, st>>>(a); break;
     default: return -1;
   }
+  return 0;
+}
+
+int launch_cg_fold(int prec, const VecArgs &a, cudaStream_t st) {
+  if (a.g.vh <= 0) return 0;
+  dim3 grid = grid_for(a.g, 256, a.nrhs);
+  if (xs_prec(prec) == PREC_F64) cg_fold_kernel<PREC_F64><<<grid, 256, 0, st>>>(a);
+  else cg_fold_kernel<PREC_F32><<<grid, 256, 0, st>>>(a);
   return 0;
 }
 

@@ -1,16 +1,21 @@
 // Driver of the batched mixed-precision CG (one system per slot).
 //
-// One iteration is six kernels, all gated on device-resident slot state so
-// that no host decision sits inside an iteration:
+// One iteration is four kernels, gated on device-resident slot state so that
+// no host decision sits inside an iteration:
 //   1. t  = D_oe p                          (sloppy Dslash)
 //   2. Ap = m^2 p - D_eo t, <p, Ap>         (sloppy Dslash + epilogue; alpha)
-//   3. x64 += alpha p, r -= alpha Ap, |r|^2 (beta, or flag a reliable update)
-//   4. t64 = D_oe x64                       (FP64, flagged slots only)
-//   5. r = b - (m^2 x64 - D_eo t64), |r|^2, <r, p>   (FP64; finishes the update)
-//   6. p = a r + beta p
-// k iterations are captured once into a CUDA graph and replayed; the host
-// reads the slot states after each replay.  Finished slots make every
-// kernel skip their work, so overshooting the last block costs launches only.
+//   3. xs += alpha p, r -= alpha Ap, |r|^2  (beta, or flag a reliable update)
+//   4. p = a r + beta p
+// and, between 3 and 4, the reliable-update body for flagged slots:
+//   R1. x64 += xs, xs = 0                   (FP64 solution accumulator)
+//   R2. t64 = D_oe x64                      (FP64 Dslash)
+//   R3. r = b - (m^2 x64 - D_eo t64), |r|^2, <r, p>   (FP64; finishes the update)
+// k iterations are captured once into a CUDA graph and replayed; in the graph
+// the body sits under an IF conditional node that kernel 3 switches on only
+// when some slot needs an update, so the FP64 kernels cost nothing otherwise.
+// The host reads the slot states after each replay.  Finished slots make
+// every kernel skip their work, so overshooting the last block costs
+// launches only.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -23,7 +28,8 @@ CGWork::~CGWork() {
   if (exec) cudaGraphExecDestroy(exec);
   if (slots_h) cudaFreeHost(slots_h);
   if (ctx) {
-    void *bufs[] = {x64, b64, t64, r, p, ap, t, slots_d, partial, counters};
+    if (body_stream) cudaStreamDestroy(body_stream);
+    void *bufs[] = {x64, b64, t64, r, p, ap, t, xs, slots_d, partial, counters};
     for (void *b : bufs)
       if (b) cudaFree(b);
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -43,12 +49,13 @@ int cg_work_create(sq_ctx *ctx, GaugeField *gf, int prec, int recon, int nrhs, C
   const Geom &g = gf->g;
   w->f64_fb = spinor_bytes(PREC_F64, g.stride);
   w->fb = spinor_bytes(prec, g.stride);
+  w->xs_fb = spinor_bytes(xs_prec(prec), g.stride);
   w->partial_stride = (size_t)3 * nrhs * g.nchunks;
   size_t sizes[] = {w->f64_fb * nrhs, w->f64_fb * nrhs, w->f64_fb * nrhs, w->fb * nrhs,
-                    w->fb * nrhs,     w->fb * nrhs,     w->fb * nrhs,
+                    w->fb * nrhs,     w->fb * nrhs,     w->fb * nrhs,     w->xs_fb * nrhs,
                     sizeof(SlotState) * nrhs, sizeof(double) * 4 * w->partial_stride,
                     sizeof(unsigned) * 8};
-  char **ptrs[] = {&w->x64, &w->b64, &w->t64, &w->r, &w->p, &w->ap, &w->t};
+  char **ptrs[] = {&w->x64, &w->b64, &w->t64, &w->r, &w->p, &w->ap, &w->t, &w->xs};
   size_t total = 0;
   for (size_t s : sizes) total += s;
   {
@@ -58,16 +65,16 @@ int cg_work_create(sq_ctx *ctx, GaugeField *gf, int prec, int recon, int nrhs, C
   }
   w->ctx = ctx;
   w->bytes = total;
-  for (int k = 0; k < 7; ++k) SQ_CUDA_TRY(cudaMalloc((void **)ptrs[k], sizes[k]));
-  SQ_CUDA_TRY(cudaMalloc((void **)&w->slots_d, sizes[7]));
-  SQ_CUDA_TRY(cudaMalloc((void **)&w->partial, sizes[8]));
-  SQ_CUDA_TRY(cudaMalloc((void **)&w->counters, sizes[9]));
-  SQ_CUDA_TRY(cudaMemset(w->counters, 0, sizes[9]));
-  SQ_CUDA_TRY(cudaMemset(w->partial, 0, sizes[8]));
-  // sloppy vectors start zeroed so no kernel reads NaN garbage from padding
-  for (int k = 3; k < 7; ++k) SQ_CUDA_TRY(cudaMemset(*ptrs[k], 0, sizes[k]));
-  SQ_CUDA_TRY(cudaMemset(w->t64, 0, sizes[2]));
-  SQ_CUDA_TRY(cudaMallocHost((void **)&w->slots_h, sizes[7]));
+  for (int k = 0; k < 8; ++k) SQ_CUDA_TRY(cudaMalloc((void **)ptrs[k], sizes[k]));
+  SQ_CUDA_TRY(cudaMalloc((void **)&w->slots_d, sizes[8]));
+  SQ_CUDA_TRY(cudaMalloc((void **)&w->partial, sizes[9]));
+  SQ_CUDA_TRY(cudaMalloc((void **)&w->counters, sizes[10]));
+  SQ_CUDA_TRY(cudaMemset(w->counters, 0, sizes[10]));
+  SQ_CUDA_TRY(cudaMemset(w->partial, 0, sizes[9]));
+  // vectors start zeroed so no kernel reads NaN garbage from padding
+  for (int k = 0; k < 8; ++k) SQ_CUDA_TRY(cudaMemset(*ptrs[k], 0, sizes[k]));
+  SQ_CUDA_TRY(cudaMallocHost((void **)&w->slots_h, sizes[8]));
+  SQ_CUDA_TRY(cudaStreamCreateWithFlags(&w->body_stream, cudaStreamNonBlocking));
   for (int k = 0; k < nrhs; ++k) {
     std::memset(&w->slots_h[k], 0, sizeof(SlotState));
     w->slots_h[k].status = SLOT_IDLE;
@@ -110,9 +117,13 @@ static VecArgs vec_args(CGWork *w, int region) {
   a.p = w->p;
   a.ap = w->ap;
   a.fb = w->fb;
+  a.xs = w->xs;
+  a.xs_fb = w->xs_fb;
   a.slots = w->slots_d;
   a.partial = w->partial + region * w->partial_stride;
   a.counter = w->counters + region;
+  a.ru_cond = 0;
+  a.set_cond = 0;
   return a;
 }
 
@@ -151,7 +162,10 @@ int cg_enqueue_init(CGWork *w, int guess, cudaStream_t st) {
 }
 
 int cg_enqueue_ru(CGWork *w, cudaStream_t st) {
-  // t64 = D_oe x64 (FP64) for slots with a pending reliable update
+  // x64 += xs, xs = 0 for slots with a pending reliable update
+  int rc0 = check_launch(w->ctx, launch_cg_fold(w->prec, vec_args(w, 1), st));
+  if (rc0) return rc0;
+  // t64 = D_oe x64 (FP64)
   DslashArgs a = dslash_args(w, PREC_F64, 18, 1);
   a.in = w->x64;
   a.in_fb = w->f64_fb;
@@ -183,7 +197,14 @@ int cg_enqueue_xpay(CGWork *w, cudaStream_t st) {
   return check_launch(w->ctx, launch_cg_xpay(w->prec, vec_args(w, 1), st));
 }
 
-int cg_enqueue_iteration(CGWork *w, cudaStream_t st) {
+int cg_enqueue_update(CGWork *w, cudaStream_t st, unsigned long long cond) {
+  VecArgs va = vec_args(w, 1);
+  va.ru_cond = cond;
+  va.set_cond = cond != 0;
+  return check_launch(w->ctx, launch_cg_update(w->prec, va, st));
+}
+
+int cg_enqueue_iteration(CGWork *w, cudaStream_t st, unsigned long long cond) {
   int rc;
   DslashArgs a = dslash_args(w, w->prec, w->recon, 1);
   a.in = w->p;
@@ -207,16 +228,74 @@ int cg_enqueue_iteration(CGWork *w, cudaStream_t st) {
   rc = check_launch(w->ctx, launch_dslash(w->prec, w->recon, w->cfg_mdagm.nr, MODE_MDAGM,
                                           w->prec, b, w->cfg_mdagm.block, st));
   if (rc) return rc;
-  VecArgs va = vec_args(w, 1);
-  if ((rc = check_launch(w->ctx, launch_cg_update(w->prec, va, st)))) return rc;
-  if ((rc = cg_enqueue_ru(w, st))) return rc;
-  return cg_enqueue_xpay(w, st);
+  if ((rc = cg_enqueue_update(w, st, cond))) return rc;
+  if (!cond && (rc = cg_enqueue_ru(w, st))) return rc;
+  return cond ? SQ_OK : cg_enqueue_xpay(w, st);
+}
+
+// Capture k iterations.  With `conditional`, each iteration's reliable-update
+// body is the child graph of an IF node whose handle the update kernel sets.
+static int capture_block(CGWork *w, int k, bool conditional, cudaStream_t st,
+                         cudaGraph_t *out) {
+  cudaGraph_t graph = nullptr;
+  SQ_CUDA_TRY(cudaGraphCreate(&graph, 0));
+  cudaError_t e = cudaStreamBeginCaptureToGraph(st, graph, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    SQ_CUDA_TRY(e);
+  }
+  int rc = SQ_OK;
+  for (int it = 0; it < k && rc == SQ_OK; ++it) {
+    if (!conditional) {
+      rc = cg_enqueue_iteration(w, st, 0);
+      continue;
+    }
+    cudaGraphConditionalHandle h = 0;
+    e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { rc = SQ_ERR_UNSUPPORTED; break; }
+    if ((rc = cg_enqueue_iteration(w, st, (unsigned long long)h))) break;
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) { rc = SQ_ERR_UNSUPPORTED; break; }
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &np);
+    if (e != cudaSuccess) { rc = SQ_ERR_UNSUPPORTED; break; }
+    e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1,
+                                            cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) { rc = SQ_ERR_UNSUPPORTED; break; }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(w->body_stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { rc = SQ_ERR_UNSUPPORTED; break; }
+    rc = cg_enqueue_ru(w, w->body_stream);
+    cudaGraph_t body_out = nullptr;
+    e = cudaStreamEndCapture(w->body_stream, &body_out);
+    if (rc == SQ_OK && e != cudaSuccess) rc = SQ_ERR_UNSUPPORTED;
+    if (rc == SQ_OK) rc = cg_enqueue_xpay(w, st);
+  }
+  cudaGraph_t g2 = nullptr;
+  e = cudaStreamEndCapture(st, &g2);
+  if (rc == SQ_OK && e != cudaSuccess) rc = conditional ? SQ_ERR_UNSUPPORTED : SQ_ERR_CUDA;
+  if (rc != SQ_OK) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return rc;
+  }
+  *out = graph;
+  return SQ_OK;
 }
 
 int cg_enqueue_block(CGWork *w, int k, bool graph, cudaStream_t st) {
   if (!graph) {
     for (int it = 0; it < k; ++it) {
-      int rc = cg_enqueue_iteration(w, st);
+      int rc = cg_enqueue_iteration(w, st, 0);
       if (rc) return rc;
     }
     return SQ_OK;
@@ -226,22 +305,36 @@ int cg_enqueue_block(CGWork *w, int k, bool graph, cudaStream_t st) {
       cudaGraphExecDestroy(w->exec);
       w->exec = nullptr;
     }
-    cudaGraph_t graph_h;
-    SQ_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     uint64_t before = w->ctx->launches.load();
-    int rc = SQ_OK;
-    for (int it = 0; it < k && rc == SQ_OK; ++it) rc = cg_enqueue_iteration(w, st);
-    cudaError_t e = cudaStreamEndCapture(st, &graph_h);
-    w->exec_kernels = (int)(w->ctx->launches.load() - before);
-    w->ctx->launches -= w->exec_kernels;  // counted when replayed
-    if (rc != SQ_OK) {
-      if (e == cudaSuccess) cudaGraphDestroy(graph_h);
-      return rc;
+    cudaGraph_t g = nullptr;
+    int rc = SQ_ERR_UNSUPPORTED;
+    bool cond = w->conditional_ok;
+    if (cond) {
+      rc = capture_block(w, k, true, st, &g);
+      if (rc == SQ_OK && cudaGraphInstantiate(&w->exec, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        w->exec = nullptr;
+        rc = SQ_ERR_UNSUPPORTED;
+      }
+      if (rc != SQ_OK) w->conditional_ok = cond = false;
     }
-    SQ_CUDA_TRY(e);
-    e = cudaGraphInstantiate(&w->exec, graph_h, 0);
-    cudaGraphDestroy(graph_h);
-    SQ_CUDA_TRY(e);
+    if (!cond) {
+      w->ctx->launches = before;
+      rc = capture_block(w, k, false, st, &g);
+      if (rc != SQ_OK) return rc;
+      cudaError_t e = cudaGraphInstantiate(&w->exec, g, 0);
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        SQ_CUDA_TRY(e);
+      }
+    }
+    cudaGraphDestroy(g);
+    // kernels outside conditional bodies run on every replay; bodies are
+    // counted from the reliable updates they perform (cg_run)
+    w->exec_kernels = cond ? 4 * k : (int)(w->ctx->launches.load() - before);
+    w->exec_conditional = cond;
+    w->ctx->launches = before;
     w->exec_iters = k;
   }
   SQ_CUDA_TRY(cudaGraphLaunch(w->exec, st));
@@ -255,14 +348,24 @@ static bool any_running(const CGWork *w) {
   return false;
 }
 
+static int total_updates(const CGWork *w) {
+  int n = 0;
+  for (int k = 0; k < w->nrhs; ++k) n += w->slots_h[k].n_ru;
+  return n;
+}
+
 int cg_run(CGWork *w, int block_iters, bool graph, cudaStream_t st) {
   int rc;
   if ((rc = cg_slots_download(w, st))) return rc;
   SQ_CUDA_TRY(cudaStreamSynchronize(st));
   while (any_running(w)) {
+    int ru0 = total_updates(w);
     if ((rc = cg_enqueue_block(w, block_iters, graph, st))) return rc;
     if ((rc = cg_slots_download(w, st))) return rc;
     SQ_CUDA_TRY(cudaStreamSynchronize(st));
+    // conditional reliable-update bodies that ran: 3 kernels each (upper
+    // bound when several slots update in the same iteration)
+    if (graph && w->exec_conditional) w->ctx->launches += 3 * (total_updates(w) - ru0);
   }
   return SQ_OK;
 }

@@ -478,18 +478,35 @@ __device__ __forceinline__ bool last_block_arrived(unsigned *counter, unsigned t
   return is_last;
 }
 
-// Fixed-order sum of n partials (strided per thread, then a shared tree).
-// All threads of the block call it; the result is valid in every thread.
+// Fixed-order sum of n partials: 128 virtual lanes (the block's first 128
+// threads) accumulate strided elements in order k, k + 128, k + 256, ...,
+// then a fixed shuffle tree and the four warp sums in order.  Independent of
+// the block size, so every configuration gives the same bits.  All threads
+// of the block call it; the result is valid in every thread.
+constexpr int SUM_LANES = 128;
+
 __device__ __forceinline__ double block_sum_fixed(const double *p, int n, double *smem) {
   double s = 0;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) s += __ldcg(p + k);
+  if (threadIdx.x < SUM_LANES) {
+    for (int k0 = threadIdx.x; k0 < n; k0 += 8 * SUM_LANES) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {  // eight loads in flight per round
+        int k = k0 + u * SUM_LANES;
+        v[u] = (k < n) ? __ldcg(p + k) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+  }
   s = warp_sum(s);
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
-  if (lane == 0) smem[warp] = s;
+  if (lane == 0 && warp < SUM_LANES / 32) smem[warp] = s;
   __syncthreads();
   double t = 0;
-  for (int w = 0; w < nw; ++w) t += smem[w];
+#pragma unroll
+  for (int w = 0; w < SUM_LANES / 32; ++w) t += smem[w];
   __syncthreads();
   return t;
 }

@@ -16,14 +16,22 @@ struct VecArgs {
   size_t f64_fb;
   char *r, *p, *ap;   // sloppy-precision fields
   size_t fb;
+  char *xs;           // solution increment since the last reliable update
+  size_t xs_fb;       // (FP32, or FP64 for plain FP64 CG)
   SlotState *slots;
   double *partial;
   unsigned *counter;
+  unsigned long long ru_cond;  // graph conditional handle set to "any reliable update"
+  int set_cond;                // 1: the update kernel sets ru_cond
 };
+
+// Precision of the solution increment for a sloppy precision.
+inline int xs_prec(int prec) { return prec == PREC_F64 ? PREC_F64 : PREC_F32; }
 
 int launch_cg_update(int prec, const VecArgs &a, cudaStream_t st);
 int launch_cg_xpay(int prec, const VecArgs &a, cudaStream_t st);
 int launch_cg_init(int prec, const VecArgs &a, int guess, cudaStream_t st);
+int launch_cg_fold(int prec, const VecArgs &a, cudaStream_t st);
 
 // canonical complex128 [i][colour] (nrhs fields, canon_elems complex apart)
 int launch_pack(int prec, const Geom &g, const double *canon, size_t canon_elems, void *out,
