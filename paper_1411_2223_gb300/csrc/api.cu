@@ -518,14 +518,7 @@ int solve_batch(sq_ctx *ctx, int gauge_id, int nrhs, const double *src, const do
   int rc;
   if ((rc = cg_slots_upload(w, st))) return rc;
   if ((rc = cg_enqueue_init(w, guess ? 1 : 0, st))) return rc;
-  // SQ_CG_GRAPH=plain|off overrides the graph form (profilers cannot see
-  // kernels inside graphs that hold conditional nodes)
-  bool use_graph = !(o.flags & SQ_CG_NO_GRAPH);
-  if (const char *gm = std::getenv("SQ_CG_GRAPH")) {
-    if (!std::strcmp(gm, "off")) use_graph = false;
-    if (!std::strcmp(gm, "plain")) w->conditional_ok = false;
-  }
-  if ((rc = cg_run(w, o.block_iters, use_graph, st))) return rc;
+  if ((rc = cg_run(w, o.block_iters, !(o.flags & SQ_CG_NO_GRAPH), st))) return rc;
   if (launch_unpack(PREC_F64, gf->g, w->x64, w->f64_fb, cx, vec_elems, nrhs, st)) return SQ_ERR_ARG;
   ctx->launches++;
   if (!dev) SQ_CUDA_TRY(cudaMemcpyAsync(x, cx, canon_bytes, cudaMemcpyDeviceToHost, st));

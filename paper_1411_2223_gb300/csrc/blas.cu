@@ -19,16 +19,11 @@ __device__ __forceinline__ bool any_running(const SlotState *s, int n) {
 }
 
 // xs += alpha p ; r -= alpha Ap ; partial |r|^2 ; last block: finish_update
-// and, inside a conditional graph, switch the reliable-update body on or off.
 template <int S>
 __global__ void __launch_bounds__(256) cg_update_kernel(VecArgs a) {
   using R = typename SpinorIO<S>::R;
   constexpr int XP = (S == PREC_F64) ? PREC_F64 : PREC_F32;
-  if (!any_running(a.slots, a.nrhs)) {
-    if (a.set_cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
-      cudaGraphSetConditional(a.ru_cond, 0u);
-    return;
-  }
+  if (!any_running(a.slots, a.nrhs)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   const int St = a.g.stride;
@@ -60,37 +55,10 @@ __global__ void __launch_bounds__(256) cg_update_kernel(VecArgs a) {
     for (int k = 0; k < a.nrhs; ++k) {
       if (!running(a.slots + k)) continue;
       double rr = block_sum_fixed(a.partial + (size_t)k * a.g.nchunks, a.g.nchunks, red);
-      if (threadIdx.x == 0) finish_update(a.slots + k, rr);
+      if (threadIdx.x == 0) finish_update(a.slots + k, rr, a.checkpoint);
     }
-    if (threadIdx.x == 0) {
-      *a.counter = 0;
-      if (a.set_cond) {
-        unsigned any = 0;
-        for (int k = 0; k < a.nrhs; ++k) any |= (a.slots[k].ru_pending != 0);
-        cudaGraphSetConditional(a.ru_cond, any);
-      }
-    }
+    if (threadIdx.x == 0) *a.counter = 0;
   }
-}
-
-// Reliable update, first step: x64 += xs, xs = 0 for the flagged systems.
-template <int XP>
-__global__ void __launch_bounds__(256) cg_fold_kernel(VecArgs a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = blockIdx.y;
-  if (i >= a.g.vh || !a.slots[r].ru_pending) return;
-  const int St = a.g.stride;
-  auto xs = SpinorIO<XP>::load(a.xs + r * a.xs_fb, St, i);
-  Vec3<double> x = SpinorIO<PREC_F64>::load(a.x64 + r * a.f64_fb, St, i);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    x.c[c].x += (double)xs.c[c].x;
-    x.c[c].y += (double)xs.c[c].y;
-  }
-  SpinorIO<PREC_F64>::store(a.x64 + r * a.f64_fb, St, i, x);
-  decltype(xs) z;
-  zero(z);
-  SpinorIO<XP>::store(a.xs + r * a.xs_fb, St, i, z);
 }
 
 // p = a r + beta p (a complex, 1 except right after a reliable update)
@@ -160,7 +128,10 @@ __global__ void __launch_bounds__(256) cg_init_kernel(VecArgs a, int guess) {
       double b2 = block_sum_fixed(a.partial + (size_t)k * a.g.nchunks, a.g.nchunks, red);
       if (threadIdx.x == 0) {
         finish_init(a.slots + k, b2);
-        if (guess && a.slots[k].status == SLOT_RUNNING) a.slots[k].ru_pending = 1;
+        if (guess && a.slots[k].status == SLOT_RUNNING) {
+          a.slots[k].ru_pending = 1;
+          a.slots[k].status = SLOT_WAIT;
+        }
       }
     }
     if (threadIdx.x == 0) *a.counter = 0;
@@ -219,14 +190,6 @@ int launch_cg_update(int prec, const VecArgs &a, cudaStream_t st) {
     case PREC_I16: cg_update_kernel<PREC_I16><<<grid, 256, 0, st>>>(a); break;
     default: return -1;
   }
-  return 0;
-}
-
-int launch_cg_fold(int prec, const VecArgs &a, cudaStream_t st) {
-  if (a.g.vh <= 0) return 0;
-  dim3 grid = grid_for(a.g, 256, a.nrhs);
-  if (xs_prec(prec) == PREC_F64) cg_fold_kernel<PREC_F64><<<grid, 256, 0, st>>>(a);
-  else cg_fold_kernel<PREC_F32><<<grid, 256, 0, st>>>(a);
   return 0;
 }
 

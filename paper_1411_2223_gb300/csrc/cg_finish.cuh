@@ -4,10 +4,10 @@
 // CG on A x = b (Hestenes-Stiefel): alpha = rr / <p, A p>, x += alpha p,
 // r -= alpha A p, beta = rr_new / rr, p = r + beta p.  The mixed-precision
 // variant (the paper's "most of the calculations in single precision", Sec. 2)
-// keeps x in FP64 and recomputes the true residual b - A x in FP64 whenever
-// |r| drops below delta * max|r| since the last update, when the recursion
-// claims convergence, and at max_iter (reliable updates).  After such an
-// update the old direction p is made orthogonal to the new residual,
+// accumulates x in FP64 and recomputes the true residual b - A x in FP64
+// when |r| has dropped below delta * max|r| since the last update, when the
+// recursion claims convergence, and at max_iter (reliable updates).  After
+// such an update the old direction p is made orthogonal to the new residual,
 // p <- p - (<r, p> / |r|^2) r, before p = r + beta p.
 #pragma once
 
@@ -47,17 +47,27 @@ __device__ __forceinline__ void finish_alpha(SlotState *s, double pap) {
   }
 }
 
-__device__ __forceinline__ void finish_update(SlotState *s, double rr_new) {
+// Reliable updates run only at checkpoints (every few iterations).  A slot
+// whose recursion claims convergence, reaches max_iter or breaks down is
+// frozen (SLOT_WAIT) until the next checkpoint decides from the FP64
+// residual; a slot whose |r| merely fell below delta * max|r| keeps iterating
+// and is updated at the next checkpoint.
+__device__ __forceinline__ void finish_update(SlotState *s, double rr_new, int checkpoint) {
   s->iter += 1;
   if (!isfinite(rr_new)) {
     s->status = SLOT_NONFINITE;
     return;
   }
   double rn = sqrt(rr_new);
-  bool ru = s->ru_pending || rr_new <= s->tol2b2 || rn < s->delta * s->maxr ||
-            s->iter >= s->max_iter;
-  if (ru) {
+  if (s->ru_pending || rr_new <= s->tol2b2 || s->iter >= s->max_iter) {
     s->ru_pending = 1;  // beta and rr come from the FP64 residual
+    s->status = SLOT_WAIT;
+    return;
+  }
+  if (rn < s->delta * s->maxr) s->ru_want = 1;
+  if (checkpoint && s->ru_want) {
+    s->ru_pending = 1;
+    s->ru_want = 0;
     return;
   }
   s->beta = rr_new / s->rr;
@@ -71,8 +81,10 @@ __device__ __forceinline__ void finish_update(SlotState *s, double rr_new) {
 __device__ __forceinline__ void finish_reliable_update(SlotState *s, double rr_true,
                                                        double rp_re, double rp_im) {
   s->ru_pending = 0;
+  s->ru_want = 0;
   s->n_ru += 1;
   s->rr_true = rr_true;
+  s->status = SLOT_RUNNING;
   if (!isfinite(rr_true)) {
     s->status = SLOT_NONFINITE;
     return;

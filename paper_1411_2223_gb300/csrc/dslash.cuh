@@ -16,8 +16,11 @@
 //               + per-chunk partials of Re<p, out>, and the last block sets
 //               alpha = rr / <p, Ap> for every running system
 //   MODE_RESID  r = b - (m^2 x - D in), FP64     (reliable update: true residual)
-//               written in the sloppy precision OUTP, + partials of |r|^2
-//               and <r, p_sloppy>; the last block finishes the update
+//               with x = x64 + xs folded into x64 first; r is written in the
+//               sloppy precision OUTP, + partials of |r|^2 and <r, p_sloppy>;
+//               the last block finishes the update
+// For a reliable update the PLAIN FP64 kernel gathers x64 + xs (the FP64
+// solution plus its sloppy increment since the previous update).
 #pragma once
 
 #include "sq_device.cuh"
@@ -44,6 +47,11 @@ struct DslashArgs {
   // RESID: FP64 x and b, sloppy p
   const char *x64, *b64;
   size_t f64_fb;
+  // reliable update: solution increment xs (precision xs_prec) added to the
+  // FP64 input at every gathered neighbour (PLAIN) or folded into x64 (RESID)
+  char *xs;
+  size_t xs_fb;
+  int xs_prec;
   const char *ps;
   size_t ps_fb;
   SlotState *slots;           // nullptr: no CG state (operator application only)
@@ -80,6 +88,33 @@ __device__ __forceinline__ Vec3<R> gather(const char *f, int S, int n, float sca
     }
     return v;
   }
+}
+
+// Neighbour input of the Dslash: the field itself, or for the FP64 operator
+// of a reliable update the FP64 solution plus its sloppy increment.
+template <int PREC, int MODE, typename R>
+__device__ __forceinline__ Vec3<R> gather_in(const char *f, const char *fx, int xs_prec, int S,
+                                             int n, float scale) {
+  if constexpr (PREC == PREC_F64 && MODE == 0) {
+    if (fx != nullptr) {
+      Vec3<double> v = SpinorIO<PREC_F64>::load(f, S, n);
+      if (xs_prec == PREC_F32) {
+        Vec3<float> d = SpinorIO<PREC_F32>::load(fx, S, n);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { v.c[c].x += (double)d.c[c].x; v.c[c].y += (double)d.c[c].y; }
+      } else {
+        Vec3<double> d = SpinorIO<PREC_F64>::load(fx, S, n);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { v.c[c].x += d.c[c].x; v.c[c].y += d.c[c].y; }
+      }
+      if (scale < 0.f) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { v.c[c].x = -v.c[c].x; v.c[c].y = -v.c[c].y; }
+      }
+      return v;
+    }
+  }
+  return gather<PREC, R>(f, S, n, scale);
 }
 
 // acc -= M v
@@ -130,6 +165,17 @@ dslash_kernel(const DslashArgs a) {
 #pragma unroll
   for (int r = 0; r < NR; ++r) zero(acc[r]);
 
+  // the epilogue's own-site operand is fetched up front so its latency hides
+  // behind the link stream
+  Vec3<R> pre[NR];
+  if constexpr (MODE == MODE_MDAGM) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (valid && active[r]) pre[r] = SpinorIO<PREC>::load(a.p + (size_t)(r0 + r) * a.p_fb, S, i);
+      else zero(pre[r]);
+    }
+  }
+
   if (valid) {
     const SiteCoords sc = site_coords(g, a.out_parity, i);
 #pragma unroll 1
@@ -151,16 +197,17 @@ dslash_kernel(const DslashArgs a) {
       for (int r = 0; r < NR; ++r) {
         if (!active[r]) continue;
         const char *f = a.in + (size_t)(r0 + r) * a.in_fb;
+        const char *fx = (a.xs != nullptr) ? a.xs + (size_t)(r0 + r) * a.xs_fb : nullptr;
         Vec3<R> t;
         zero(t);
         Vec3<R> v;
-        v = gather<PREC, R>(f, S, nb[0], sg[0]);
+        v = gather_in<PREC, MODE, R>(f, fx, a.xs_prec, S, nb[0], sg[0]);
         mat_vec_acc(t, m[0], v);
-        v = gather<PREC, R>(f, S, nb[1], sg[1]);
+        v = gather_in<PREC, MODE, R>(f, fx, a.xs_prec, S, nb[1], sg[1]);
         mat_vec_sub(t, m[1], v);
-        v = gather<PREC, R>(f, S, nb[2], sg[2]);
+        v = gather_in<PREC, MODE, R>(f, fx, a.xs_prec, S, nb[2], sg[2]);
         mat_vec_acc(t, m[2], v);
-        v = gather<PREC, R>(f, S, nb[3], sg[3]);
+        v = gather_in<PREC, MODE, R>(f, fx, a.xs_prec, S, nb[3], sg[3]);
         mat_vec_sub(t, m[3], v);
         if (eta > 0.f) {
 #pragma unroll
@@ -192,7 +239,7 @@ dslash_kernel(const DslashArgs a) {
       dot[r] = 0.0;
       if (valid && active[r]) {
         const R m2 = (R)(a.slots ? a.slots[r0 + r].m2 : a.m2_const);
-        Vec3<R> p = SpinorIO<PREC>::load(a.p + (size_t)(r0 + r) * a.p_fb, S, i);
+        const Vec3<R> &p = pre[r];
         Vec3<R> o;
         R d = 0;
 #pragma unroll
@@ -228,6 +275,23 @@ dslash_kernel(const DslashArgs a) {
       if (valid && active[r]) {
         const double m2 = a.slots[r0 + r].m2;
         Vec3<double> x = SpinorIO<PREC_F64>::load(a.x64 + (size_t)(r0 + r) * a.f64_fb, S, i);
+        if (a.xs != nullptr) {  // fold the sloppy increment: x64 += xs, xs = 0
+          char *fx = a.xs + (size_t)(r0 + r) * a.xs_fb;
+          if (a.xs_prec == PREC_F32) {
+            Vec3<float> d = SpinorIO<PREC_F32>::load(fx, S, i), z;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) { x.c[c].x += (double)d.c[c].x; x.c[c].y += (double)d.c[c].y; }
+            zero(z);
+            SpinorIO<PREC_F32>::store(fx, S, i, z);
+          } else {
+            Vec3<double> d = SpinorIO<PREC_F64>::load(fx, S, i), z;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) { x.c[c].x += d.c[c].x; x.c[c].y += d.c[c].y; }
+            zero(z);
+            SpinorIO<PREC_F64>::store(fx, S, i, z);
+          }
+          SpinorIO<PREC_F64>::store(const_cast<char *>(a.x64) + (size_t)(r0 + r) * a.f64_fb, S, i, x);
+        }
         Vec3<double> b = SpinorIO<PREC_F64>::load(a.b64 + (size_t)(r0 + r) * a.f64_fb, S, i);
         Vec3<double> rr;
 #pragma unroll

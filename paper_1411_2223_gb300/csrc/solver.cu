@@ -6,16 +6,16 @@
 //   2. Ap = m^2 p - D_eo t, <p, Ap>         (sloppy Dslash + epilogue; alpha)
 //   3. xs += alpha p, r -= alpha Ap, |r|^2  (beta, or flag a reliable update)
 //   4. p = a r + beta p
-// and, between 3 and 4, the reliable-update body for flagged slots:
-//   R1. x64 += xs, xs = 0                   (FP64 solution accumulator)
-//   R2. t64 = D_oe x64                      (FP64 Dslash)
-//   R3. r = b - (m^2 x64 - D_eo t64), |r|^2, <r, p>   (FP64; finishes the update)
-// k iterations are captured once into a CUDA graph and replayed; in the graph
-// the body sits under an IF conditional node that kernel 3 switches on only
-// when some slot needs an update, so the FP64 kernels cost nothing otherwise.
-// The host reads the slot states after each replay.  Finished slots make
-// every kernel skip their work, so overshooting the last block costs
-// launches only.
+// and after every RU_PERIOD-th iteration (a checkpoint) the reliable-update
+// pair, which does work only for flagged slots:
+//   R1. t64 = D_oe (x64 + xs)               (FP64 Dslash)
+//   R2. x64 += xs, xs = 0; r = b - (m^2 x64 - D_eo t64), |r|^2, <r, p>
+//                                           (FP64 Dslash + epilogue; finishes it)
+// Checkpoints keep the FP64 kernels' launch cost off most iterations; a slot
+// that wants to stop waits frozen for the next checkpoint, so no iteration is
+// wasted.  k iterations are captured once into a CUDA graph and replayed; the
+// host reads the slot states after each replay.  Finished slots make every
+// kernel skip their work, so overshooting the last block costs launches only.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -28,7 +28,6 @@ CGWork::~CGWork() {
   if (exec) cudaGraphExecDestroy(exec);
   if (slots_h) cudaFreeHost(slots_h);
   if (ctx) {
-    if (body_stream) cudaStreamDestroy(body_stream);
     void *bufs[] = {x64, b64, t64, r, p, ap, t, xs, slots_d, partial, counters};
     for (void *b : bufs)
       if (b) cudaFree(b);
@@ -74,7 +73,6 @@ int cg_work_create(sq_ctx *ctx, GaugeField *gf, int prec, int recon, int nrhs, C
   // vectors start zeroed so no kernel reads NaN garbage from padding
   for (int k = 0; k < 8; ++k) SQ_CUDA_TRY(cudaMemset(*ptrs[k], 0, sizes[k]));
   SQ_CUDA_TRY(cudaMallocHost((void **)&w->slots_h, sizes[8]));
-  SQ_CUDA_TRY(cudaStreamCreateWithFlags(&w->body_stream, cudaStreamNonBlocking));
   for (int k = 0; k < nrhs; ++k) {
     std::memset(&w->slots_h[k], 0, sizeof(SlotState));
     w->slots_h[k].status = SLOT_IDLE;
@@ -122,8 +120,7 @@ static VecArgs vec_args(CGWork *w, int region) {
   a.slots = w->slots_d;
   a.partial = w->partial + region * w->partial_stride;
   a.counter = w->counters + region;
-  a.ru_cond = 0;
-  a.set_cond = 0;
+  a.checkpoint = 0;
   return a;
 }
 
@@ -162,20 +159,20 @@ int cg_enqueue_init(CGWork *w, int guess, cudaStream_t st) {
 }
 
 int cg_enqueue_ru(CGWork *w, cudaStream_t st) {
-  // x64 += xs, xs = 0 for slots with a pending reliable update
-  int rc0 = check_launch(w->ctx, launch_cg_fold(w->prec, vec_args(w, 1), st));
-  if (rc0) return rc0;
-  // t64 = D_oe x64 (FP64)
+  // t64 = D_oe (x64 + xs) in FP64 for slots with a pending reliable update
   DslashArgs a = dslash_args(w, PREC_F64, 18, 1);
   a.in = w->x64;
   a.in_fb = w->f64_fb;
+  a.xs = w->xs;
+  a.xs_fb = w->xs_fb;
+  a.xs_prec = xs_prec(w->prec);
   a.out = w->t64;
   a.out_fb = w->f64_fb;
   a.gate = GATE_RU;
   int rc = check_launch(w->ctx, launch_dslash(PREC_F64, 18, w->cfg_ru_plain.nr, MODE_PLAIN,
                                               PREC_F64, a, w->cfg_ru_plain.block, st));
   if (rc) return rc;
-  // r = b - (m^2 x64 - D_eo t64) -> sloppy r ; |r|^2, <r, p>
+  // x64 += xs, xs = 0; r = b - (m^2 x64 - D_eo t64) -> sloppy r ; |r|^2, <r, p>
   DslashArgs b = dslash_args(w, PREC_F64, 18, 0);
   b.in = w->t64;
   b.in_fb = w->f64_fb;
@@ -184,6 +181,9 @@ int cg_enqueue_ru(CGWork *w, cudaStream_t st) {
   b.x64 = w->x64;
   b.b64 = w->b64;
   b.f64_fb = w->f64_fb;
+  b.xs = w->xs;
+  b.xs_fb = w->xs_fb;
+  b.xs_prec = xs_prec(w->prec);
   b.ps = w->p;
   b.ps_fb = w->fb;
   b.partial = w->partial + 2 * w->partial_stride;
@@ -197,14 +197,7 @@ int cg_enqueue_xpay(CGWork *w, cudaStream_t st) {
   return check_launch(w->ctx, launch_cg_xpay(w->prec, vec_args(w, 1), st));
 }
 
-int cg_enqueue_update(CGWork *w, cudaStream_t st, unsigned long long cond) {
-  VecArgs va = vec_args(w, 1);
-  va.ru_cond = cond;
-  va.set_cond = cond != 0;
-  return check_launch(w->ctx, launch_cg_update(w->prec, va, st));
-}
-
-int cg_enqueue_iteration(CGWork *w, cudaStream_t st, unsigned long long cond) {
+int cg_enqueue_iteration(CGWork *w, cudaStream_t st, int checkpoint) {
   int rc;
   DslashArgs a = dslash_args(w, w->prec, w->recon, 1);
   a.in = w->p;
@@ -228,74 +221,18 @@ int cg_enqueue_iteration(CGWork *w, cudaStream_t st, unsigned long long cond) {
   rc = check_launch(w->ctx, launch_dslash(w->prec, w->recon, w->cfg_mdagm.nr, MODE_MDAGM,
                                           w->prec, b, w->cfg_mdagm.block, st));
   if (rc) return rc;
-  if ((rc = cg_enqueue_update(w, st, cond))) return rc;
-  if (!cond && (rc = cg_enqueue_ru(w, st))) return rc;
-  return cond ? SQ_OK : cg_enqueue_xpay(w, st);
-}
-
-// Capture k iterations.  With `conditional`, each iteration's reliable-update
-// body is the child graph of an IF node whose handle the update kernel sets.
-static int capture_block(CGWork *w, int k, bool conditional, cudaStream_t st,
-                         cudaGraph_t *out) {
-  cudaGraph_t graph = nullptr;
-  SQ_CUDA_TRY(cudaGraphCreate(&graph, 0));
-  cudaError_t e = cudaStreamBeginCaptureToGraph(st, graph, nullptr, nullptr, 0,
-                                                cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) {
-    cudaGraphDestroy(graph);
-    SQ_CUDA_TRY(e);
-  }
-  int rc = SQ_OK;
-  for (int it = 0; it < k && rc == SQ_OK; ++it) {
-    if (!conditional) {
-      rc = cg_enqueue_iteration(w, st, 0);
-      continue;
-    }
-    cudaGraphConditionalHandle h = 0;
-    e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault);
-    if (e != cudaSuccess) { rc = SQ_ERR_UNSUPPORTED; break; }
-    if ((rc = cg_enqueue_iteration(w, st, (unsigned long long)h))) break;
-    cudaStreamCaptureStatus cs;
-    const cudaGraphNode_t *deps = nullptr;
-    size_t ndeps = 0;
-    e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
-    if (e != cudaSuccess) { rc = SQ_ERR_UNSUPPORTED; break; }
-    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
-    np.conditional.handle = h;
-    np.conditional.type = cudaGraphCondTypeIf;
-    np.conditional.size = 1;
-    cudaGraphNode_t node;
-    e = cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &np);
-    if (e != cudaSuccess) { rc = SQ_ERR_UNSUPPORTED; break; }
-    e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1,
-                                            cudaStreamSetCaptureDependencies);
-    if (e != cudaSuccess) { rc = SQ_ERR_UNSUPPORTED; break; }
-    cudaGraph_t body = np.conditional.phGraph_out[0];
-    e = cudaStreamBeginCaptureToGraph(w->body_stream, body, nullptr, nullptr, 0,
-                                      cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) { rc = SQ_ERR_UNSUPPORTED; break; }
-    rc = cg_enqueue_ru(w, w->body_stream);
-    cudaGraph_t body_out = nullptr;
-    e = cudaStreamEndCapture(w->body_stream, &body_out);
-    if (rc == SQ_OK && e != cudaSuccess) rc = SQ_ERR_UNSUPPORTED;
-    if (rc == SQ_OK) rc = cg_enqueue_xpay(w, st);
-  }
-  cudaGraph_t g2 = nullptr;
-  e = cudaStreamEndCapture(st, &g2);
-  if (rc == SQ_OK && e != cudaSuccess) rc = conditional ? SQ_ERR_UNSUPPORTED : SQ_ERR_CUDA;
-  if (rc != SQ_OK) {
-    cudaGetLastError();
-    cudaGraphDestroy(graph);
-    return rc;
-  }
-  *out = graph;
-  return SQ_OK;
+  VecArgs va = vec_args(w, 1);
+  va.checkpoint = checkpoint;
+  if ((rc = check_launch(w->ctx, launch_cg_update(w->prec, va, st)))) return rc;
+  if (checkpoint && (rc = cg_enqueue_ru(w, st))) return rc;
+  return cg_enqueue_xpay(w, st);
 }
 
 int cg_enqueue_block(CGWork *w, int k, bool graph, cudaStream_t st) {
+  // reliable updates can follow every RU_PERIOD-th iteration of a block
   if (!graph) {
     for (int it = 0; it < k; ++it) {
-      int rc = cg_enqueue_iteration(w, st, 0);
+      int rc = cg_enqueue_iteration(w, st, (it + 1) % RU_PERIOD == 0);
       if (rc) return rc;
     }
     return SQ_OK;
@@ -307,34 +244,21 @@ int cg_enqueue_block(CGWork *w, int k, bool graph, cudaStream_t st) {
     }
     uint64_t before = w->ctx->launches.load();
     cudaGraph_t g = nullptr;
-    int rc = SQ_ERR_UNSUPPORTED;
-    bool cond = w->conditional_ok;
-    if (cond) {
-      rc = capture_block(w, k, true, st, &g);
-      if (rc == SQ_OK && cudaGraphInstantiate(&w->exec, g, 0) != cudaSuccess) {
-        cudaGetLastError();
-        cudaGraphDestroy(g);
-        w->exec = nullptr;
-        rc = SQ_ERR_UNSUPPORTED;
-      }
-      if (rc != SQ_OK) w->conditional_ok = cond = false;
+    SQ_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc = SQ_OK;
+    for (int it = 0; it < k && rc == SQ_OK; ++it)
+      rc = cg_enqueue_iteration(w, st, (it + 1) % RU_PERIOD == 0);
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    w->exec_kernels = (int)(w->ctx->launches.load() - before);
+    w->ctx->launches = before;  // counted on replay
+    if (rc != SQ_OK) {
+      if (e == cudaSuccess) cudaGraphDestroy(g);
+      return rc;
     }
-    if (!cond) {
-      w->ctx->launches = before;
-      rc = capture_block(w, k, false, st, &g);
-      if (rc != SQ_OK) return rc;
-      cudaError_t e = cudaGraphInstantiate(&w->exec, g, 0);
-      if (e != cudaSuccess) {
-        cudaGraphDestroy(g);
-        SQ_CUDA_TRY(e);
-      }
-    }
+    SQ_CUDA_TRY(e);
+    e = cudaGraphInstantiate(&w->exec, g, 0);
     cudaGraphDestroy(g);
-    // kernels outside conditional bodies run on every replay; bodies are
-    // counted from the reliable updates they perform (cg_run)
-    w->exec_kernels = cond ? 4 * k : (int)(w->ctx->launches.load() - before);
-    w->exec_conditional = cond;
-    w->ctx->launches = before;
+    SQ_CUDA_TRY(e);
     w->exec_iters = k;
   }
   SQ_CUDA_TRY(cudaGraphLaunch(w->exec, st));
@@ -344,28 +268,20 @@ int cg_enqueue_block(CGWork *w, int k, bool graph, cudaStream_t st) {
 
 static bool any_running(const CGWork *w) {
   for (int k = 0; k < w->nrhs; ++k)
-    if (w->slots_h[k].status == SLOT_RUNNING) return true;
+    if (w->slots_h[k].status == SLOT_RUNNING || w->slots_h[k].status == SLOT_WAIT) return true;
   return false;
-}
-
-static int total_updates(const CGWork *w) {
-  int n = 0;
-  for (int k = 0; k < w->nrhs; ++k) n += w->slots_h[k].n_ru;
-  return n;
 }
 
 int cg_run(CGWork *w, int block_iters, bool graph, cudaStream_t st) {
   int rc;
+  // whole checkpoint periods per block
+  block_iters = (block_iters + RU_PERIOD - 1) / RU_PERIOD * RU_PERIOD;
   if ((rc = cg_slots_download(w, st))) return rc;
   SQ_CUDA_TRY(cudaStreamSynchronize(st));
   while (any_running(w)) {
-    int ru0 = total_updates(w);
     if ((rc = cg_enqueue_block(w, block_iters, graph, st))) return rc;
     if ((rc = cg_slots_download(w, st))) return rc;
     SQ_CUDA_TRY(cudaStreamSynchronize(st));
-    // conditional reliable-update bodies that ran: 3 kernels each (upper
-    // bound when several slots update in the same iteration)
-    if (graph && w->exec_conditional) w->ctx->launches += 3 * (total_updates(w) - ru0);
   }
   return SQ_OK;
 }
@@ -375,7 +291,8 @@ int slot_status_to_sq(int s) {
     case SLOT_CONVERGED: return SQ_OK;
     case SLOT_MAXITER: return SQ_NOT_CONVERGED;
     case SLOT_NONFINITE: return SQ_ERR_NONFINITE;
-    case SLOT_RUNNING: return SQ_PENDING;
+    case SLOT_RUNNING:
+    case SLOT_WAIT: return SQ_PENDING;
     default: return SQ_ERR_ARG;
   }
 }

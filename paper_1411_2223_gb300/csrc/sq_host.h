@@ -102,10 +102,7 @@ struct CGWork {
   size_t partial_stride = 0;  // doubles per reduction region
   cudaGraphExec_t exec = nullptr;
   int exec_iters = 0;
-  int exec_kernels = 0;       // kernels per replay outside conditional bodies
-  bool exec_conditional = false;
-  bool conditional_ok = true; // conditional graph nodes usable on this driver
-  cudaStream_t body_stream = nullptr;
+  int exec_kernels = 0;       // kernels per replay
   DslashConfig cfg_plain, cfg_mdagm, cfg_ru_plain, cfg_ru_resid;
 
   ~CGWork();
@@ -120,10 +117,9 @@ int cg_slots_download(CGWork *w, cudaStream_t st);
 int cg_enqueue_init(CGWork *w, int guess, cudaStream_t st);
 int cg_enqueue_ru(CGWork *w, cudaStream_t st);
 int cg_enqueue_xpay(CGWork *w, cudaStream_t st);
-// One iteration; with cond != 0 the update kernel sets the graph conditional
-// `cond` and the reliable-update kernels are left to the caller.
-int cg_enqueue_iteration(CGWork *w, cudaStream_t st, unsigned long long cond = 0);
-int cg_enqueue_update(CGWork *w, cudaStream_t st, unsigned long long cond);
+// Reliable updates may follow every RU_PERIOD-th iteration (a checkpoint).
+constexpr int RU_PERIOD = 4;
+int cg_enqueue_iteration(CGWork *w, cudaStream_t st, int checkpoint);
 // k iterations: a CUDA graph replay (captured on first use) or direct launches.
 int cg_enqueue_block(CGWork *w, int k, bool graph, cudaStream_t st);
 // Run until no slot is running; host polls the slot state after each block.

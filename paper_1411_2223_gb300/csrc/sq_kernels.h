@@ -21,8 +21,7 @@ struct VecArgs {
   SlotState *slots;
   double *partial;
   unsigned *counter;
-  unsigned long long ru_cond;  // graph conditional handle set to "any reliable update"
-  int set_cond;                // 1: the update kernel sets ru_cond
+  int checkpoint;     // update kernel: a reliable update may follow this iteration
 };
 
 // Precision of the solution increment for a sloppy precision.
@@ -31,7 +30,6 @@ inline int xs_prec(int prec) { return prec == PREC_F64 ? PREC_F64 : PREC_F32; }
 int launch_cg_update(int prec, const VecArgs &a, cudaStream_t st);
 int launch_cg_xpay(int prec, const VecArgs &a, cudaStream_t st);
 int launch_cg_init(int prec, const VecArgs &a, int guess, cudaStream_t st);
-int launch_cg_fold(int prec, const VecArgs &a, cudaStream_t st);
 
 // canonical complex128 [i][colour] (nrhs fields, canon_elems complex apart)
 int launch_pack(int prec, const Geom &g, const double *canon, size_t canon_elems, void *out,

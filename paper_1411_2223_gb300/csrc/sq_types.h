@@ -33,6 +33,7 @@ enum SlotStatus {
   SLOT_MAXITER = 2,
   SLOT_NONFINITE = 3,
   SLOT_IDLE = 4,  // no system in this slot
+  SLOT_WAIT = 5,  // frozen until the next reliable-update checkpoint decides
 };
 
 struct SlotState {
@@ -50,8 +51,8 @@ struct SlotState {
   int max_iter;
   int n_ru;
   int status;       // SlotStatus
-  int ru_pending;   // FP64 true residual to be recomputed in this iteration
-  int pad;
+  int ru_pending;   // FP64 true residual to be recomputed at this checkpoint
+  int ru_want;      // |r| fell below delta * max|r|: update at the next checkpoint
 };
 
 }  // namespace sq
