@@ -464,17 +464,21 @@ __device__ __forceinline__ void chunk_reduce(double (&val)[NV], double *smem, do
 }
 
 // Returns true in every thread of the block that finished last (of `total`
-// blocks sharing `counter`); that block then sees all partials.
+// blocks sharing `counter`); that block then sees all partials.  The ticket
+// is one acquire-release atomic: release publishes this block's partials
+// (made visible to thread 0 by the barrier), acquire makes every other
+// block's partials visible to the last one -- no sequentially consistent
+// device fence per block.
 __device__ __forceinline__ bool last_block_arrived(unsigned *counter, unsigned total) {
   __shared__ bool is_last;
   __syncthreads();
   if (threadIdx.x == 0 && threadIdx.y == 0) {
-    __threadfence();
-    unsigned ticket = atomicAdd(counter, 1u);
+    unsigned ticket;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                 : "=r"(ticket) : "l"(counter), "r"(1u) : "memory");
     is_last = (ticket == total - 1);
   }
   __syncthreads();
-  if (is_last) __threadfence();
   return is_last;
 }
 

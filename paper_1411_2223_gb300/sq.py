@@ -245,7 +245,7 @@ class Context:
         o.stream = _stream(stream)
         return o
 
-    def cg_solve(self, gauge_id, src, mass, tol, precision='f32', long_recon=18, delta=0.1,
+    def cg_solve(self, gauge_id, src, mass, tol, precision='f32', long_recon=18, delta=-1.0,
                  max_iter=100000, block_iters=16, x0=None, graph=True, stream=None,
                  check=True, out=None):
         """Solve (m^2 - D_eo D_oe) x = src.  Returns (x, stats dict).
@@ -261,7 +261,7 @@ class Context:
         return xs[0], st[0]
 
     def cg_solve_multi(self, gauge_id, srcs, masses, tol, precision='f32', long_recon=18,
-                       delta=0.1, max_iter=100000, block_iters=16, x0=None, graph=True,
+                       delta=-1.0, max_iter=100000, block_iters=16, x0=None, graph=True,
                        stream=None, check=True, out=None):
         """Batched solve; returns (x (nrhs, Vh, 3), [stats dicts], status).
 
@@ -298,7 +298,7 @@ class Context:
         return x, [s.as_dict() for s in stats], status
 
     def cg_solve_multishift(self, gauge_id, src, masses, tol, precision='f32', long_recon=18,
-                            delta=0.1, max_iter=100000, block_iters=16, stream=None, check=True):
+                            delta=-1.0, max_iter=100000, block_iters=16, stream=None, check=True):
         """Multi-shift solve; returns (x (nshift, Vh, 3), [stats dicts], status)."""
         dev = _is_device(src)
         ns = len(masses)

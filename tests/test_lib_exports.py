@@ -50,7 +50,7 @@ def test_host_only_calls_without_gpu(lib):
     o = sq.CgOpts()
     l.sq_cg_opts_default(ctypes.byref(o))
     assert (o.precision, o.long_recon, o.max_iter, o.block_iters) == (1, 18, 100000, 16)
-    assert abs(o.delta - 0.1) < 1e-15
+    assert o.delta < 0  # precision-dependent default
     # argument checks fail before touching a device
     assert l.gauge_load(None, None, None, None, 0, None) == sq.ERR_ARG
     assert l.sq_destroy(None) == sq.ERR_ARG
