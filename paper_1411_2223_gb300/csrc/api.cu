@@ -142,6 +142,7 @@ extern "C" int sq_destroy(sq_ctx *ctx) {
       g_cache.erase(it);
     }
   }
+  drop_multishift_works(ctx, -1);
   std::vector<int> ids;
   for (auto &kv : ctx->gauges) ids.push_back(kv.first);
   for (int id : ids) gauge_free(ctx, id);
@@ -315,6 +316,7 @@ extern "C" int gauge_free(sq_ctx *ctx, int gauge_id) {
   if (!gf) return SQ_ERR_NOTFOUND;
   if (ctx->serve && serve_uses_gauge(ctx->serve, gauge_id)) return SQ_ERR_BUSY;
   drop_gauge_works(ctx, gauge_id);
+  drop_multishift_works(ctx, gauge_id);
   if (gf->users.load() > 0) return SQ_ERR_BUSY;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
@@ -440,9 +442,11 @@ extern "C" int mdagm_apply(sq_ctx *ctx, int gauge_id, int prec, int long_recon, 
 
 namespace sq {
 
-// Shared body of cg_solve / cg_solve_multi / the refinement of multi-shift.
-int solve_batch(sq_ctx *ctx, int gauge_id, int nrhs, const double *src, const double *masses,
-                double tol, const sq_cg_opts *opts_in, double *x, sq_cg_stats *stats) {
+// Shared body of cg_solve / cg_solve_multi / the refinement of multi-shift;
+// the caller holds ctx->solve_mu.
+int solve_batch_locked(sq_ctx *ctx, int gauge_id, int nrhs, const double *src,
+                       const double *masses, double tol, const sq_cg_opts *opts_in, double *x,
+                       sq_cg_stats *stats) {
   if (!ctx || !src || !masses || !x || nrhs < 1 || nrhs > 64) return SQ_ERR_ARG;
   if (!(tol > 0) || !std::isfinite(tol)) return SQ_ERR_ARG;
   for (int k = 0; k < nrhs; ++k)
@@ -462,7 +466,6 @@ int solve_batch(sq_ctx *ctx, int gauge_id, int nrhs, const double *src, const do
   const size_t vec_elems = (size_t)3 * gf->g.vh;  // complex per vector
   if (!dev && !finite_all(src, vec_elems * 2 * nrhs)) return SQ_ERR_NONFINITE;
 
-  std::lock_guard<std::mutex> solve_lock(ctx->solve_mu);
   cudaSetDevice(ctx->device);
   auto t0 = std::chrono::steady_clock::now();
   // Run on the caller's stream unless it is a default stream (those cannot
@@ -486,7 +489,7 @@ int solve_batch(sq_ctx *ctx, int gauge_id, int nrhs, const double *src, const do
     int rc = cg_work_create(ctx, gf, o.precision, o.long_recon, nrhs, &w);
     if (rc) return rc;
     w->cfg_plain = tuned_dslash(ctx, *gf, o.precision, o.long_recon, nrhs, MODE_PLAIN, st);
-    w->cfg_mdagm = w->cfg_plain;
+    w->cfg_mdagm = tuned_dslash(ctx, *gf, o.precision, o.long_recon, nrhs, MODE_MDAGM, st);
     w->cfg_ru_plain = tuned_dslash(ctx, *gf, PREC_F64, 18, nrhs, MODE_PLAIN, st);
     w->cfg_ru_resid = w->cfg_ru_plain;
     std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -534,6 +537,13 @@ int solve_batch(sq_ctx *ctx, int gauge_id, int nrhs, const double *src, const do
     if (s == SQ_NOT_CONVERGED) not_conv = true;
   }
   return first_err != SQ_OK ? first_err : not_conv ? SQ_NOT_CONVERGED : SQ_OK;
+}
+
+int solve_batch(sq_ctx *ctx, int gauge_id, int nrhs, const double *src, const double *masses,
+                double tol, const sq_cg_opts *opts, double *x, sq_cg_stats *stats) {
+  if (!ctx) return SQ_ERR_ARG;
+  std::lock_guard<std::mutex> solve_lock(ctx->solve_mu);
+  return solve_batch_locked(ctx, gauge_id, nrhs, src, masses, tol, opts, x, stats);
 }
 
 }  // namespace sq

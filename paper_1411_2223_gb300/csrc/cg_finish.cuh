@@ -105,4 +105,56 @@ __device__ __forceinline__ void finish_reliable_update(SlotState *s, double rr_t
   s->maxr = sqrt(rr_true);
 }
 
+// Multi-shift CG (Jegerlehner, hep-lat/9612014): with base coefficients
+// alpha_k, beta_k and alpha_{-1} = 1, beta_{-1} = 0, zeta_{-1} = zeta_0 = 1,
+//   zeta_{k+1} = zeta_k zeta_{k-1} alpha_{k-1} /
+//                (alpha_k beta_{k-1} (zeta_{k-1} - zeta_k)
+//                 + zeta_{k-1} alpha_{k-1} (1 + sigma alpha_k)),
+//   alpha^s_k = alpha_k zeta_{k+1} / zeta_k,  beta^s_k = beta_k (zeta_{k+1} / zeta_k)^2,
+//   x^s += alpha^s_k p^s,  p^s = zeta_{k+1} r_{k+1} + beta^s_k p^s.
+// Called after alpha_k of the base system is known.
+__device__ __forceinline__ void finish_shift_alpha(SlotState *b, ShiftState *sh, int n) {
+  const double al = b->alpha;
+  for (int i = 0; i < n; ++i) {
+    ShiftState &s = sh[i];
+    if (!s.active) continue;
+    double den = al * b->beta_prev * (s.zeta_prev - s.zeta) +
+                 s.zeta_prev * b->alpha_prev * (1.0 + s.sigma * al);
+    s.zeta_next = s.zeta * s.zeta_prev * b->alpha_prev / den;
+    s.alpha = al * s.zeta_next / s.zeta;
+  }
+}
+
+// After |r_{k+1}|^2: beta of every shift, per-shift convergence, rotation of
+// the zeta history.  The base keeps iterating while any shift continues.
+__device__ __forceinline__ void finish_shift_update(SlotState *b, ShiftState *sh, int n,
+                                                    double rr_new) {
+  b->iter += 1;
+  if (!isfinite(rr_new) || !isfinite(b->alpha)) {
+    b->status = SLOT_NONFINITE;
+    return;
+  }
+  const double beta = rr_new / b->rr;
+  bool any = false;
+  for (int i = 0; i < n; ++i) {
+    ShiftState &s = sh[i];
+    if (!s.active) continue;
+    double ratio = s.zeta_next / s.zeta;
+    s.beta = beta * ratio * ratio;
+    s.iter = b->iter;
+    s.cont = !(s.zeta_next * s.zeta_next * rr_new <= s.tol2b2);
+    s.zeta_prev = s.zeta;
+    s.zeta = s.zeta_next;
+    any |= s.cont != 0;
+  }
+  b->alpha_prev = b->alpha;
+  b->beta_prev = beta;
+  b->beta = beta;
+  b->rr = rr_new;
+  if (!any || b->iter >= b->max_iter) {
+    b->final_status = any ? SLOT_MAXITER : SLOT_CONVERGED;
+    b->status = SLOT_WAIT;  // the last x updates are still to be applied
+  }
+}
+
 }  // namespace sq

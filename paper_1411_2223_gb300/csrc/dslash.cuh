@@ -55,6 +55,8 @@ struct DslashArgs {
   const char *ps;
   size_t ps_fb;
   SlotState *slots;           // nullptr: no CG state (operator application only)
+  ShiftState *shifts;         // multi-shift CG: shifted systems updated with alpha
+  int nshift;
   double *partial;            // [value][rhs][chunk]
   unsigned *counter;
   int gate;
@@ -262,7 +264,10 @@ dslash_kernel(const DslashArgs a) {
         for (int r = 0; r < a.nrhs; ++r) {
           if (!slot_active(a.slots + r, a.gate)) continue;
           double pap = block_sum_fixed(a.partial + (size_t)r * g.nchunks, g.nchunks, red);
-          if (threadIdx.x == 0) finish_alpha(a.slots + r, pap);
+          if (threadIdx.x == 0) {
+            finish_alpha(a.slots + r, pap);
+            if (a.shifts) finish_shift_alpha(a.slots + r, a.shifts, a.nshift);
+          }
         }
         if (threadIdx.x == 0) *a.counter = 0;
       }

@@ -19,7 +19,3 @@ extern "C" int serve_poll(sq_ctx *, uint64_t, double *, sq_cg_stats *, int) {
 extern "C" int serve_cancel(sq_ctx *, uint64_t) { return SQ_ERR_UNSUPPORTED; }
 extern "C" int serve_stats(sq_ctx *, sq_serve_stats *, int) { return SQ_ERR_UNSUPPORTED; }
 extern "C" int serve_configure(sq_ctx *, int, int) { return SQ_ERR_UNSUPPORTED; }
-extern "C" int cg_solve_multishift(sq_ctx *, int, const double *, int, const double *, double,
-                                   const sq_cg_opts *, double *, sq_cg_stats *) {
-  return SQ_ERR_UNSUPPORTED;
-}

@@ -53,6 +53,23 @@ struct SlotState {
   int status;       // SlotStatus
   int ru_pending;   // FP64 true residual to be recomputed at this checkpoint
   int ru_want;      // |r| fell below delta * max|r|: update at the next checkpoint
+  // multi-shift CG (base system): previous-iteration coefficients
+  double alpha_prev, beta_prev;
+  int final_status;  // status taken once the last shifted updates are applied
+  int pad;
+};
+
+// Per-shift state of multi-shift CG: (A + sigma) x = b shares the Krylov
+// space of A; its residual is zeta * r.
+struct ShiftState {
+  double sigma;                   // m_i^2 - m_base^2 (>= 0)
+  double zeta, zeta_prev, zeta_next;
+  double alpha, beta;             // shifted CG coefficients of this iteration
+  double tol2b2;                  // stop once zeta^2 |r|^2 <= tol^2 |b|^2
+  int active;                     // x_i += alpha_i p_i in this iteration
+  int cont;                       // p_i continues after this iteration
+  int iter;                       // iterations this shift took
+  int pad;
 };
 
 }  // namespace sq

@@ -25,10 +25,10 @@ struct Tuner {
   std::string path;
 };
 
-static std::string tune_key(const Geom &g, int prec, int recon, int nrhs) {
+static std::string tune_key(const Geom &g, int prec, int recon, int nrhs, int mode) {
   std::ostringstream s;
-  s << "dslash_v1:" << g.L[0] << "x" << g.L[1] << "x" << g.L[2] << "x" << g.L[3] << ":p" << prec
-    << ":r" << recon << ":n" << nrhs;
+  s << "dslash_v2:" << g.L[0] << "x" << g.L[1] << "x" << g.L[2] << "x" << g.L[3] << ":p" << prec
+    << ":r" << recon << ":n" << nrhs << ":m" << mode;
   return s.str();
 }
 
@@ -55,13 +55,15 @@ static void tuner_save(Tuner *t) {
 
 DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon, int nrhs,
                           int mode, cudaStream_t st) {
-  (void)mode;  // epilogues add little traffic: one shape per (lattice, prec, recon, nrhs)
+  // PLAIN and MDAGM are tuned apart: the reduction epilogue of MDAGM favours
+  // more, smaller blocks per SM.  RESID uses the PLAIN shape.
+  if (mode != MODE_MDAGM) mode = MODE_PLAIN;
   DslashConfig def;
   def.block = 256;
   def.nr = nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1;
   Tuner *t = ctx->tuner;
   if (!t || !gf.has(prec, recon)) return def;
-  const std::string key = tune_key(gf.g, prec, recon, nrhs);
+  const std::string key = tune_key(gf.g, prec, recon, nrhs, mode);
   std::lock_guard<std::mutex> lk(t->mu);
   auto it = t->cache.find(key);
   if (it != t->cache.end()) return it->second;
@@ -71,13 +73,31 @@ DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon
 
   const Geom &g = gf.g;
   size_t fb = spinor_bytes(prec, g.stride);
-  void *in = nullptr, *out = nullptr;
+  void *in = nullptr, *out = nullptr, *aux = nullptr;
+  // aux: p field, slot states, partial sums and the ticket counter (MDAGM)
+  size_t aux_b = fb * nrhs + sizeof(SlotState) * nrhs + sizeof(double) * nrhs * g.nchunks + 256;
   if (cudaMalloc(&in, fb * nrhs) != cudaSuccess) return def;
-  if (cudaMalloc(&out, fb * nrhs) != cudaSuccess) {
+  if (cudaMalloc(&out, fb * nrhs) != cudaSuccess || cudaMalloc(&aux, aux_b) != cudaSuccess) {
     cudaFree(in);
+    if (out) cudaFree(out);
     return def;
   }
   cudaMemsetAsync(in, 0, fb * nrhs, st);
+  cudaMemsetAsync(aux, 0, aux_b, st);
+  char *auxc = static_cast<char *>(aux);
+  SlotState *slots = reinterpret_cast<SlotState *>(auxc + fb * nrhs);
+  double *partial = reinterpret_cast<double *>(slots + nrhs);
+  unsigned *counter = reinterpret_cast<unsigned *>(partial + (size_t)nrhs * g.nchunks);
+  if (mode == MODE_MDAGM) {
+    std::vector<SlotState> hs(nrhs);
+    for (auto &s : hs) {
+      std::memset(&s, 0, sizeof(s));
+      s.status = SLOT_RUNNING;
+      s.m2 = 1e-4;
+      s.rr = 1.0;
+    }
+    cudaMemcpyAsync(slots, hs.data(), sizeof(SlotState) * nrhs, cudaMemcpyHostToDevice, st);
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -92,6 +112,16 @@ DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon
   a.in_fb = a.out_fb = fb;
   a.nrhs = nrhs;
   a.gate = GATE_NONE;
+  if (mode == MODE_MDAGM) {
+    a.out_parity = 0;
+    a.links = gf.link_ptr(prec, recon, 0);
+    a.p = auxc;
+    a.p_fb = fb;
+    a.slots = slots;
+    a.partial = partial;
+    a.counter = counter;
+    a.gate = GATE_RUNNING;
+  }
   std::vector<int> nrs = {1};
   if (nrhs >= 2) nrs.push_back(2);
   if (nrhs >= 4) nrs.push_back(4);
@@ -100,9 +130,9 @@ DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon
   const int reps = 5;
   for (int nr : nrs) {
     for (int block = 128; block <= 512; block += 128) {
-      if (launch_dslash(prec, recon, nr, MODE_PLAIN, prec, a, block, st) != 0) continue;
+      if (launch_dslash(prec, recon, nr, mode, prec, a, block, st) != 0) continue;
       cudaEventRecord(e0, st);
-      for (int k = 0; k < reps; ++k) launch_dslash(prec, recon, nr, MODE_PLAIN, prec, a, block, st);
+      for (int k = 0; k < reps; ++k) launch_dslash(prec, recon, nr, mode, prec, a, block, st);
       cudaEventRecord(e1, st);
       if (cudaEventSynchronize(e1) != cudaSuccess) continue;
       float ms = 0;
@@ -119,6 +149,7 @@ DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon
   cudaEventDestroy(e1);
   cudaFree(in);
   cudaFree(out);
+  cudaFree(aux);
   t->cache[key] = best_c;
   tuner_save(t);
   return best_c;

@@ -1,0 +1,114 @@
+"""Batched (multi-RHS) and multi-shift solves vs the FP64 oracle.
+
+Every system of a batch, and every shift, passes the same acceptance as a
+single solve: the oracle's FP64 residual <= tol, |A (x - x_ref)|/|b| <= 10 tol
+and |x - x_ref| <= (|r| + |r_ref|)/m^2 against the oracle's own solution.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import gauge, o9_check
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize('prec,recon', [('f32', 18), ('f32', 12), ('i16', 12), ('f64', 18)])
+@pytest.mark.parametrize('nrhs', [3, 4, 5])
+def test_multi_rhs_matches_oracle(sq, prec, recon, nrhs):
+    dims = (4, 6, 8, 10)
+    fat, lng = gauge(dims, 0.25, 0)
+    vh = oracle.volume(dims) // 2
+    srcs = synth.gaussian_sources(vh, range(nrhs))
+    masses = np.linspace(0.03, 0.1, nrhs)
+    tol = 1e-8
+    gid = sq.gauge_load(dims, fat, lng)
+    try:
+        xs, stats, status = sq.cg_solve_multi(gid, srcs, masses, tol, precision=prec,
+                                              long_recon=recon)
+        assert status == 0
+        for j in range(nrhs):
+            assert stats[j]['status'] == 0
+            x_ref, it, _ = oracle.cg(dims, fat, lng, masses[j], srcs[j], 1e-12)
+            o9_check(dims, fat, lng, masses[j], srcs[j], xs[j], x_ref, tol)
+            # the batched system followed its own recursion: same iteration
+            # count as solving it alone
+            x1, st1 = sq.cg_solve(gid, srcs[j], masses[j], tol, precision=prec, long_recon=recon)
+            assert abs(st1['iterations'] - stats[j]['iterations']) <= 4
+    finally:
+        sq.gauge_free(gid)
+
+
+def test_multi_rhs_mixed_convergence_and_zero_source(sq):
+    """Systems finish at different iterations; a zero source finishes at once."""
+    dims = (8, 4, 4, 8)
+    fat, lng = gauge(dims, 0.25, 0)
+    vh = oracle.volume(dims) // 2
+    srcs = synth.gaussian_sources(vh, [1, 2, 3])
+    srcs[1] = 0
+    masses = [0.01, 0.05, 0.3]
+    gid = sq.gauge_load(dims, fat, lng)
+    try:
+        xs, stats, status = sq.cg_solve_multi(gid, srcs, masses, 1e-9)
+        assert status == 0
+        assert stats[1]['iterations'] == 0 and np.all(xs[1] == 0)
+        assert stats[2]['iterations'] < stats[0]['iterations']
+        for j in (0, 2):
+            assert oracle.true_residual(dims, fat, lng, masses[j], srcs[j], xs[j]) <= 1e-9
+    finally:
+        sq.gauge_free(gid)
+
+
+@pytest.mark.parametrize('prec', ['f32', 'i16', 'f64'])
+def test_multishift_matches_oracle(sq, prec):
+    dims = (4, 4, 4, 8)
+    fat, lng = gauge(dims, 0.25, 0)
+    vh = oracle.volume(dims) // 2
+    b = synth.gaussian_source(vh, 0)
+    # 8 masses from 0.005 to 0.1, geometric, smallest not first
+    masses = 0.005 * 20.0 ** (np.arange(8) / 7.0)
+    masses = masses[[3, 0, 7, 1, 6, 2, 5, 4]]
+    tol = 1e-8
+    gid = sq.gauge_load(dims, fat, lng)
+    try:
+        xs, stats, status = sq.cg_solve_multishift(gid, b, masses, tol, precision=prec)
+        assert status == 0
+        xo, it_o, tr_o = oracle.cg_multishift(dims, fat, lng, masses, b, 1e-12)
+        for i, m in enumerate(masses):
+            assert stats[i]['status'] == 0
+            o9_check(dims, fat, lng, m, b, xs[i], xo[i], tol)
+        # the heaviest shift converges in fewer Krylov steps than the lightest
+        assert stats[int(np.argmax(masses))]['iterations'] < stats[int(np.argmin(masses))]['iterations']
+    finally:
+        sq.gauge_free(gid)
+
+
+def test_multishift_single_mass_equals_cg(sq):
+    dims = (8, 4, 4, 4)
+    fat, lng = gauge(dims, 0.25, 0)
+    b = synth.gaussian_source(oracle.volume(dims) // 2, 3)
+    gid = sq.gauge_load(dims, fat, lng)
+    try:
+        xs, stats, status = sq.cg_solve_multishift(gid, b, [0.05], 1e-9, precision='f64')
+        assert status == 0
+        assert oracle.true_residual(dims, fat, lng, 0.05, b, xs[0]) <= 1e-9
+    finally:
+        sq.gauge_free(gid)
+
+
+def test_multishift_device_pointers(sq):
+    import torch
+    dims = (4, 4, 8, 8)
+    fat, lng = gauge(dims, 0.25, 0)
+    b = synth.gaussian_source(oracle.volume(dims) // 2, 5)
+    masses = [0.02, 0.04, 0.08]
+    gid = sq.gauge_load(dims, fat, lng)
+    try:
+        xd, sd, _ = sq.cg_solve_multishift(gid, torch.from_numpy(b).cuda(), masses, 1e-8)
+        xh, sh, _ = sq.cg_solve_multishift(gid, b, masses, 1e-8)
+        assert np.array_equal(xd.cpu().numpy(), xh)
+        for i, m in enumerate(masses):
+            assert oracle.true_residual(dims, fat, lng, m, b, xh[i]) <= 1e-8
+    finally:
+        sq.gauge_free(gid)
