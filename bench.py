@@ -188,6 +188,18 @@ def config_dict():
 
 # ------------------------------------------------------------------- GPU arm
 
+def max_over_ranks(value, dist=None):
+    """Slowest replica's value (replicas only: no data-path collective; this
+    one all-reduce of a scalar happens after the timed region)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    dev = 'cuda' if dist.get_backend() == 'nccl' else 'cpu'
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def time_dslash(ctx, gid, b_dev, stream, vh, formats, iters):
     """Average device time per Dslash launch (CUDA events on the launching
     stream), alternating output parities so both link fields stream from HBM."""
@@ -291,11 +303,7 @@ def main():
         ev1.synchronize()
     launches = ctx.kernel_launches() - l0
     barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device='cuda')
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist)
     iters = st['iterations']
     clk = clocks.summary()
 
