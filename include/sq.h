@@ -170,6 +170,25 @@ int dslash_apply(sq_ctx *ctx, int gauge_id, int out_parity, int prec, int long_r
 int mdagm_apply(sq_ctx *ctx, int gauge_id, int prec, int long_recon, double mass,
                 const void *in_dev, void *out_dev, void *stream);
 
+/* Same operator as mdagm_apply, for callers that must not allocate device
+ * memory at call time: work recorded into a CUDA graph by stream capture,
+ * applications that reserve all of HBM through their own allocator or pool,
+ * latency-critical loops that cannot take a first-use cudaMalloc.  (The paper
+ * has no counterpart; this is an interface of this library only.)
+ * The odd-parity temporary lives in one fixed device array of
+ * SQ_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits; the call allocates nothing (no cudaMalloc, no tuning).
+ * The packed vector of one parity (sq_spinor_bytes) must fit that array --
+ * e.g. up to 524288 sites per parity in FP32 (a 20^3 x 64 lattice has
+ * 256000) -- otherwise SQ_ERR_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the array and the temporary is fully
+ * rewritten by each call, but calls that overlap on the GPU (other streams,
+ * other threads) race on it: serialise them.  in/out as for mdagm_apply. */
+#define SQ_STATIC_SCRATCH_BYTES (12u << 20)
+int mdagm_apply_static(sq_ctx *ctx, int gauge_id, int prec, int long_recon, double mass,
+                       const void *in_dev, void *out_dev, void *stream);
+
 /* ---- solvers -------------------------------------------------------------- */
 
 /* Solve (m^2 - D_eo D_oe) x = b to |b - A x| / |b| <= tol: CG in the sloppy

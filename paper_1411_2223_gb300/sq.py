@@ -34,6 +34,7 @@ GAUGE_NO_F64 = 0x80
 CG_DEVICE_PTRS = 0x1
 CG_INITIAL_GUESS = 0x2
 CG_NO_GRAPH = 0x4
+STATIC_SCRATCH_BYTES = 12 << 20   # SQ_STATIC_SCRATCH_BYTES of include/sq.h
 
 
 class SqError(RuntimeError):
@@ -86,6 +87,7 @@ SIGNATURES = {
     'sq_unpack_spinor': (_I, [_P, _I, _I, _P, _P, _P]),
     'dslash_apply': (_I, [_P, _I, _I, _I, _I, _P, _P, _P]),
     'mdagm_apply': (_I, [_P, _I, _I, _I, _D, _P, _P, _P]),
+    'mdagm_apply_static': (_I, [_P, _I, _I, _I, _D, _P, _P, _P]),
     'cg_solve': (_I, [_P, _I, _P, _D, _D, ctypes.POINTER(CgOpts), _P, ctypes.POINTER(CgStats)]),
     'cg_solve_multi': (_I, [_P, _I, _I, _P, _P, _D, ctypes.POINTER(CgOpts), _P,
                             ctypes.POINTER(CgStats)]),
@@ -231,6 +233,14 @@ class Context:
         _check(self._lib.mdagm_apply(self.handle, gauge_id, PREC[prec], int(long_recon),
                                      float(mass), _ptr(in_dev), _ptr(out_dev), _stream(stream)),
                'mdagm_apply')
+
+    def mdagm_apply_static(self, gauge_id, prec, long_recon, mass, in_dev, out_dev,
+                           stream=None):
+        """mdagm_apply with the temporary in the library's fixed device array
+        (no allocation; for callers that cannot allocate at call time)."""
+        _check(self._lib.mdagm_apply_static(self.handle, gauge_id, PREC[prec], int(long_recon),
+                                            float(mass), _ptr(in_dev), _ptr(out_dev),
+                                            _stream(stream)), 'mdagm_apply_static')
 
     # --------------------------------------------------------------- solvers
     def _opts(self, precision, long_recon, delta, max_iter, block_iters, flags, stream):
