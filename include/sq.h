@@ -118,8 +118,9 @@ typedef struct {
 /* ---- context -------------------------------------------------------------- */
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
- * memory the context may hold (gauge fields + solver workspaces); 0 = 90% of
- * the device's free memory.  Returns SQ_ERR_CUDA without a usable device. */
+ * memory the context may hold (gauge fields + solver and serving workspaces;
+ * not the transient staging of gauge_load); 0 = 90% of the device's free
+ * memory.  Returns SQ_ERR_CUDA without a usable device. */
 int sq_create(sq_ctx **out, int device, size_t hbm_budget_bytes);
 int sq_destroy(sq_ctx *ctx);
 const char *sq_strerror(int status);

@@ -218,7 +218,12 @@ extern "C" int gauge_load(sq_ctx *ctx, const int dims[4], const double *fat, con
   if (!(flags & SQ_GAUGE_DEVICE_PTRS)) {
     if (!finite_all(fat, (size_t)vol * 72) || !finite_all(lng, (size_t)vol * 72))
       return SQ_ERR_NONFINITE;
-    if ((rc = ctx->alloc(2 * nlink_bytes, &tmp))) return rc;
+    // staging of the canonical links, freed before return: outside the budget
+    cudaError_t ae = cudaMalloc(&tmp, 2 * nlink_bytes);
+    if (ae != cudaSuccess) {
+      set_last_cuda_error(ae, "cudaMalloc(link staging)", __FILE__, __LINE__);
+      return SQ_ERR_OOM;
+    }
     dfat = static_cast<double *>(tmp);
     dlng = dfat + (size_t)vol * 72;
     cudaMemcpyAsync((void *)dfat, fat, nlink_bytes, cudaMemcpyHostToDevice, st);
@@ -251,7 +256,7 @@ extern "C" int gauge_load(sq_ctx *ctx, const int dims[4], const double *fat, con
   }
   if (e != cudaSuccess) {
     set_last_cuda_error(e, "gauge statistics", __FILE__, __LINE__);
-    ctx->release(tmp, 2 * nlink_bytes);
+    if (tmp) cudaFree(tmp);
     return SQ_ERR_CUDA;
   }
   double fmax_, lmax_, rerr;
@@ -259,7 +264,7 @@ extern "C" int gauge_load(sq_ctx *ctx, const int dims[4], const double *fat, con
   std::memcpy(&lmax_, &stats_h[1], 8);
   std::memcpy(&rerr, &stats_h[2], 8);
   if (!std::isfinite(fmax_) || !std::isfinite(lmax_)) {
-    ctx->release(tmp, 2 * nlink_bytes);
+    if (tmp) cudaFree(tmp);
     return SQ_ERR_NONFINITE;
   }
   gf->fat_scale = (float)fmax_;
@@ -289,7 +294,7 @@ extern "C" int gauge_load(sq_ctx *ctx, const int dims[4], const double *fat, con
     }
   }
   e = cudaStreamSynchronize(st);
-  if (tmp) ctx->release(tmp, 2 * nlink_bytes);
+  if (tmp) cudaFree(tmp);
   if (rc == SQ_OK && e != cudaSuccess) {
     set_last_cuda_error(e, "gauge pack", __FILE__, __LINE__);
     rc = SQ_ERR_CUDA;

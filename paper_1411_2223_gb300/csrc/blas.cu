@@ -83,8 +83,10 @@ __global__ void __launch_bounds__(256) cg_xpay_kernel(VecArgs a) {
   SpinorIO<S>::store(a.p + r * a.fb, St, i, p);
 }
 
-// Start of a solve: r = b (sloppy), p = r, x64 = 0; or with an initial guess
-// p = 0 and a pending FP64 residual.  Partial |b|^2; last block: finish_init.
+// Start of the systems in SLOT_INIT: r = b (sloppy), p = r, x64 = 0; or with
+// an initial guess p = 0 and a pending FP64 residual.  Partial |b|^2; last
+// block: finish_init.  Slots already iterating are left alone, so systems
+// can join a running batch.
 template <int S>
 __global__ void __launch_bounds__(256) cg_init_kernel(VecArgs a, int guess) {
   using R = typename SpinorIO<S>::R;
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(256) cg_init_kernel(VecArgs a, int guess) {
   const int r = blockIdx.y;
   const int St = a.g.stride;
   SlotState *s = a.slots + r;
-  const bool act = running(s);
+  const bool act = s->status == SLOT_INIT;
   double val[1] = {0.0};
   if (i < a.g.vh && act) {
     Vec3<double> b = SpinorIO<PREC_F64>::load(a.b64 + r * a.f64_fb, St, i);
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(256) cg_init_kernel(VecArgs a, int guess) {
   if (last_block_arrived(a.counter, gridDim.x * gridDim.y)) {
     __shared__ double red[32];
     for (int k = 0; k < a.nrhs; ++k) {
-      if (!running(a.slots + k)) continue;
+      if (a.slots[k].status != SLOT_INIT) continue;
       double b2 = block_sum_fixed(a.partial + (size_t)k * a.g.nchunks, a.g.nchunks, red);
       if (threadIdx.x == 0) {
         finish_init(a.slots + k, b2);

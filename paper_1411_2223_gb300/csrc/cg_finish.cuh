@@ -16,6 +16,7 @@
 namespace sq {
 
 __device__ __forceinline__ void finish_init(SlotState *s, double b2) {
+  s->status = SLOT_RUNNING;
   s->b2 = b2;
   s->tol2b2 = s->tol2 * b2;
   s->rr = b2;

@@ -88,7 +88,7 @@ void cg_slot_setup(CGWork *w, int slot, double mass, double tol, double delta, i
   s.tol2 = tol * tol;
   s.delta = (w->prec == PREC_F64) ? 0.0 : delta;
   s.max_iter = max_iter;
-  s.status = SLOT_RUNNING;
+  s.status = SLOT_INIT;
   s.a_re = 1.0;
 }
 
@@ -268,7 +268,7 @@ int cg_enqueue_block(CGWork *w, int k, bool graph, cudaStream_t st) {
 
 static bool any_running(const CGWork *w) {
   for (int k = 0; k < w->nrhs; ++k)
-    if (w->slots_h[k].status == SLOT_RUNNING || w->slots_h[k].status == SLOT_WAIT) return true;
+    if (cg_slot_live(w->slots_h[k].status)) return true;
   return false;
 }
 
@@ -292,7 +292,8 @@ int slot_status_to_sq(int s) {
     case SLOT_MAXITER: return SQ_NOT_CONVERGED;
     case SLOT_NONFINITE: return SQ_ERR_NONFINITE;
     case SLOT_RUNNING:
-    case SLOT_WAIT: return SQ_PENDING;
+    case SLOT_WAIT:
+    case SLOT_INIT: return SQ_PENDING;
     default: return SQ_ERR_ARG;
   }
 }

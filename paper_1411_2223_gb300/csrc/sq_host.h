@@ -125,6 +125,7 @@ int cg_enqueue_block(CGWork *w, int k, bool graph, cudaStream_t st);
 // Run until no slot is running; host polls the slot state after each block.
 int cg_run(CGWork *w, int block_iters, bool graph, cudaStream_t st);
 int slot_status_to_sq(int slot_status);
+inline bool cg_slot_live(int s) { return s == SLOT_RUNNING || s == SLOT_WAIT || s == SLOT_INIT; }
 void drop_multishift_works(const sq_ctx *ctx, int gauge_id);  // gauge_id < 0: all
 void fill_stats(const SlotState &s, double seconds, long vh, sq_cg_stats *st);
 

@@ -34,6 +34,7 @@ enum SlotStatus {
   SLOT_NONFINITE = 3,
   SLOT_IDLE = 4,  // no system in this slot
   SLOT_WAIT = 5,  // frozen until the next reliable-update checkpoint decides
+  SLOT_INIT = 6,  // admitted; the init kernel starts it
 };
 
 struct SlotState {
