@@ -53,6 +53,8 @@ def parse_args():
                    help='seconds of oracle work in the CPU baseline sample')
     p.add_argument('--no-cpu-baseline', action='store_true')
     p.add_argument('--dslash-iters', type=int, default=200)
+    p.add_argument('--serve-requests', type=int, default=2000,
+                   help='requests in the serving run (0: skip it)')
     p.add_argument('--dslash-only', default=None, metavar='FORMATS',
                    help='profiling aid: only time the Dslash in these formats '
                         '(comma list of prec_recon, e.g. f32_18), no solves')
@@ -187,6 +189,83 @@ def config_dict():
 
 
 # ------------------------------------------------------------------- GPU arm
+
+# Serving workload: volumes drawn uniformly from four resident gauge fields
+# (seeds 1..4), am ~ U[0.005, 0.05], tol in {1e-6, 1e-8}; a pool of eight
+# Gaussian sources per field (seed 10000*field + k) is cycled through.
+SERVE_FIELDS = [((8, 8, 8, 8), 1), ((16, 16, 16, 32), 2), ((20, 20, 20, 64), 3),
+                ((24, 24, 24, 48), 4)]
+
+
+def serve_bench(ctx, n_req, sq):
+    """Closed-loop throughput, then Poisson arrivals at 0.8x that rate."""
+    import threading
+    import numpy as np
+    import synth
+    flags = sq.GAUGE_NO_I16 | sq.GAUGE_NO_LONG12
+    gids, pools = [], []
+    for dims, seed in SERVE_FIELDS:
+        fat, lng = synth.gauge_field(dims, EPS, seed)
+        gids.append(ctx.gauge_load(dims, fat, lng, flags=flags))
+        vh = int(np.prod(dims)) // 2
+        pools.append([synth.gaussian_source(vh, 10000 * seed + k) for k in range(8)])
+        del fat, lng
+    rng = np.random.default_rng(7)
+    reqs = [(int(f), float(m), float(t)) for f, m, t in
+            zip(rng.integers(0, 4, n_req), rng.uniform(0.005, 0.05, n_req),
+                np.array([1e-6, 1e-8])[rng.integers(0, 2, n_req)])]
+    ctx.serve_configure(slots_per_batch=8, block_iters=8)
+
+    def submit(i):
+        f, m, t = reqs[i]
+        return ctx.serve_submit(gids[f], pools[f][i % 8], m, t)
+
+    # warm-up: tuning and graph capture of every field's batch
+    for t in [ctx.serve_submit(g, pools[k][0], 0.02, 1e-6) for k, g in enumerate(gids)]:
+        ctx.serve_poll(t, timeout_us=-1, want_x=False)
+    ctx.serve_stats(reset=True)
+    t0 = time.time()
+    tickets = [submit(i) for i in range(n_req)]
+    bad = sum(ctx.serve_poll(t, timeout_us=-1, want_x=False)[0] != 0 for t in tickets)
+    closed_s = time.time() - t0
+    closed = ctx.serve_stats(reset=True)
+    rate = 0.8 * n_req / closed_s
+    gaps = rng.exponential(1.0 / rate, n_req)
+    done = []
+
+    def poller(tks):
+        for t in tks:
+            done.append(ctx.serve_poll(t, timeout_us=-1, want_x=False)[0])
+    tks = []
+    th = None
+    t0 = time.time()
+    due = t0
+    for i in range(n_req):
+        due += gaps[i]
+        dt = due - time.time()
+        if dt > 0:
+            time.sleep(dt)
+        tks.append(submit(i))
+    th = threading.Thread(target=poller, args=(tks,))
+    th.start()
+    th.join()
+    open_s = time.time() - t0
+    st = ctx.serve_stats()
+    bad += sum(x != 0 for x in done)
+    for g in gids:
+        ctx.gauge_free(g)
+    return {'requests': n_req, 'failed': int(bad),
+            'workload': 'volumes uniform over 8^4, 16^3x32, 20^3x64, 24^3x48 (4 resident '
+                        'fields), am ~ U[0.005,0.05], tol in {1e-6,1e-8}, 8 slots per field, '
+                        'FP32 CG + FP64 reliable updates',
+            'closed_loop': {'solves_per_s': round(n_req / closed_s, 2),
+                            'p50_ms': round(closed['p50_ms'], 2),
+                            'p99_ms': round(closed['p99_ms'], 2)},
+            'open_loop': {'arrival_rate_hz': round(rate, 2), 'seconds': round(open_s, 2),
+                          'p50_ms': round(st['p50_ms'], 2), 'p99_ms': round(st['p99_ms'], 2),
+                          'mean_ms': round(st['mean_ms'], 2),
+                          'solves_per_s': round(st['solves_per_s'], 2)}}
+
 
 def max_over_ranks(value, dist=None):
     """Slowest replica's value (replicas only: no data-path collective; this
@@ -362,6 +441,8 @@ def main():
                 'peak_kind': peak_kind + ' (MEASURED_PEAKS.json hbm_gbs, burst)'
                 if peak_kind == 'measured' else 'fallback'}
 
+    serve = serve_bench(ctx, args.serve_requests, sq) if args.serve_requests > 0 else None
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(fat, lng, b_host, args.cpu_sample_s)
@@ -383,6 +464,7 @@ def main():
                        'reliable_updates': st16['reliable_updates'],
                        'true_residual': st16['true_residual'], 'long_recon': 12},
             'dslash': dslash,
+            'serve': serve,
             'roofline': roofline,
             'e2e': {'value': round(ms_e2e, 3), 'unit': 'ms', 'h2d_bytes_per_step': h2d,
                     'd2h_bytes_per_step': d2h},
