@@ -134,8 +134,14 @@ __device__ __forceinline__ void mat_vec_sub(Vec3<R> &acc, const Mat3<R> &m, cons
   }
 }
 
+// Launch bounds per precision: FP64 needs the large register file of the SM
+// (a 512-thread bound squeezes it to 64 registers and spills); FP32 and
+// 16-bit fit 128 registers at up to 512 threads.
+template <int PREC> struct DslashBounds { static constexpr int threads = 512, min_blocks = 1; };
+template <> struct DslashBounds<PREC_F64> { static constexpr int threads = 256, min_blocks = 1; };
+
 template <int PREC, int RECON, int NR, int MODE, int OUTP>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(DslashBounds<PREC>::threads, DslashBounds<PREC>::min_blocks)
 dslash_kernel(const DslashArgs a) {
   using R = typename AccumType<PREC>::R;
   const Geom &g = a.g;
