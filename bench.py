@@ -55,9 +55,13 @@ def parse_args():
     p.add_argument('--dslash-iters', type=int, default=200)
     p.add_argument('--serve-requests', type=int, default=2000,
                    help='requests in the serving run (0: skip it)')
+    p.add_argument('--no-extra', action='store_true',
+                   help='skip the 32^3x64 16-bit and 24^3x64 batched workloads')
     p.add_argument('--dslash-only', default=None, metavar='FORMATS',
                    help='profiling aid: only time the Dslash in these formats '
                         '(comma list of prec_recon, e.g. f32_18), no solves')
+    p.add_argument('--dims', default=None, metavar='LX,LY,LZ,LT',
+                   help='lattice of the --dslash-only run (default 20,20,20,64)')
     return p.parse_args()
 
 
@@ -267,6 +271,113 @@ def serve_bench(ctx, n_req, sq):
                           'solves_per_s': round(st['solves_per_s'], 2)}}
 
 
+# 16-bit workload: 32^3 x 64, eps 0.25, am 0.01, tol 1e-8, 16-bit storage with
+# per-site norms, 12-real long links, FP32 accumulation, FP64 reliable updates.
+I16_DIMS = (32, 32, 32, 64)
+# Batched workload: 24^3 x 64, eps 0.25; 12 Gaussian sources (seeds 0..11) at
+# am 0.01 in one multi-RHS solve, and 8 masses am = 0.005 * 20^(i/7) from one
+# source (seed 0) in one multi-shift solve; tol 1e-8, FP32 + FP64 reliable updates.
+BATCH_DIMS = (24, 24, 24, 64)
+BATCH_NRHS = 12
+
+
+def timed(fn, stream, reps=1):
+    """Device time per call of fn (CUDA events on `stream`) and fn's last result."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def i16_workload(ctx, sq, stream, dslash_iters):
+    """32^3 x 64 in 16-bit storage: solve time, FP64 error against the plain
+    FP64 GPU CG solution, and the 16-bit Dslash throughput at this volume."""
+    import numpy as np
+    import torch
+    import synth
+    dims = I16_DIMS
+    vh = int(np.prod(dims)) // 2
+    fat, lng = synth.gauge_field(dims, EPS, GAUGE_SEED)
+    gid = ctx.gauge_load(dims, fat, lng, flags=sq.GAUGE_NO_F32)
+    del fat, lng
+    b = torch.from_numpy(synth.gaussian_source(vh, SRC_SEED)).cuda()
+    x = torch.empty_like(b)
+
+    def solve(prec, recon):
+        return ctx.cg_solve(gid, b, MASS, TOL, precision=prec, long_recon=recon, stream=stream,
+                            out=x)[1]
+    solve('i16', 12)
+    ms16, st16 = timed(lambda: solve('i16', 12), stream, 2)
+    x16 = x.clone()
+    ms64, st64 = timed(lambda: solve('f64', 18), stream, 1)
+    err = float(torch.linalg.vector_norm(x16 - x) / torch.linalg.vector_norm(x))
+    dsl = time_dslash(ctx, gid, b, stream, vh, (('i16', 12), ('i16', 18)), dslash_iters)
+    ctx.gauge_free(gid)
+    return {'workload': '32^3x64 (eps 0.25 synthetic links, seed 0), am 0.01, tol 1e-8, 16-bit '
+                        'storage + per-site norms, 12-real long links, FP32 accumulate, FP64 '
+                        'reliable updates',
+            'ms': round(ms16, 3), 'iterations': st16['iterations'],
+            'reliable_updates': st16['reliable_updates'],
+            'true_residual': st16['true_residual'],
+            'fp64_cg_ms': round(ms64, 3), 'fp64_cg_iterations': st64['iterations'],
+            'speedup_vs_fp64': round(ms64 / ms16, 3),
+            'fp64_error_vs_fp64_cg': err, 'dslash': dsl}
+
+
+def batched_workload(ctx, sq, stream):
+    """24^3 x 64: 12 right-hand sides in one batched solve against 12 single
+    solves, and 8 masses in one multi-shift solve against 8 single solves."""
+    import numpy as np
+    import torch
+    import synth
+    dims = BATCH_DIMS
+    vh = int(np.prod(dims)) // 2
+    fat, lng = synth.gauge_field(dims, EPS, GAUGE_SEED)
+    gid = ctx.gauge_load(dims, fat, lng, flags=sq.GAUGE_NO_I16 | sq.GAUGE_NO_LONG12)
+    del fat, lng
+    srcs = torch.from_numpy(synth.gaussian_sources(vh, range(BATCH_NRHS))).cuda()
+    xs = torch.empty_like(srcs)
+    masses = [MASS] * BATCH_NRHS
+    shifts = list(0.005 * 20.0 ** (np.arange(8) / 7.0))
+
+    def multi():
+        return ctx.cg_solve_multi(gid, srcs, masses, TOL, stream=stream, out=xs)[1]
+
+    def singles(sources, ms):
+        return [ctx.cg_solve(gid, s, m, TOL, stream=stream, out=xs[0])[1]
+                for s, m in zip(sources, ms)]
+
+    def mshift():
+        return ctx.cg_solve_multishift(gid, srcs[0], shifts, TOL, stream=stream)[1]
+    multi()
+    ms_multi, st_multi = timed(multi, stream)
+    singles(srcs[:1], masses[:1])
+    ms_single, st_single = timed(lambda: singles(srcs, masses), stream)
+    mshift()
+    ms_shift, st_shift = timed(mshift, stream)
+    ms_shift_single, _ = timed(lambda: singles([srcs[0]] * len(shifts), shifts), stream)
+    ctx.gauge_free(gid)
+    worst = max(s['true_residual'] for s in st_multi + st_shift)
+    return {'workload': '24^3x64 (eps 0.25 synthetic links, seed 0), tol 1e-8, FP32 + FP64 '
+                        'reliable updates: 12 sources (seeds 0..11) at am 0.01 batched; 8 masses '
+                        'am = 0.005*20^(i/7) multi-shift from source seed 0',
+            'multi_rhs': {'rhs': BATCH_NRHS, 'ms': round(ms_multi, 3),
+                          'ms_per_solve': round(ms_multi / BATCH_NRHS, 3),
+                          'single_solves_ms': round(ms_single, 3),
+                          'speedup_vs_single': round(ms_single / ms_multi, 3),
+                          'iterations_max': max(s['iterations'] for s in st_multi)},
+            'multi_shift': {'shifts': len(shifts), 'ms': round(ms_shift, 3),
+                            'single_solves_ms': round(ms_shift_single, 3),
+                            'speedup_vs_single': round(ms_shift_single / ms_shift, 3),
+                            'iterations': [s['iterations'] for s in st_shift]},
+            'worst_true_residual': worst}
+
+
 def max_over_ranks(value, dist=None):
     """Slowest replica's value (replicas only: no data-path collective; this
     one all-reduce of a scalar happens after the timed region)."""
@@ -327,9 +438,12 @@ def main():
         import torch.distributed as dist
         dist.init_process_group('nccl' if torch.cuda.is_available() else 'gloo')
     torch.cuda.set_device(local)
-    vh = int(np.prod(DIMS)) // 2
+    dims = DIMS
+    if args.dslash_only and args.dims:
+        dims = tuple(int(v) for v in args.dims.split(','))
+    vh = int(np.prod(dims)) // 2
 
-    fat, lng = synth.gauge_field(DIMS, EPS, GAUGE_SEED)
+    fat, lng = synth.gauge_field(dims, EPS, GAUGE_SEED)
     b_host = synth.gaussian_source(vh, SRC_SEED)
     ctx = sq.Context(local)
     gflags = 0
@@ -343,7 +457,7 @@ def main():
             gflags |= sq.GAUGE_NO_I16
         if not any(f.endswith('_12') for f in want):
             gflags |= sq.GAUGE_NO_LONG12
-    gid = ctx.gauge_load(DIMS, fat, lng, flags=gflags)
+    gid = ctx.gauge_load(dims, fat, lng, flags=gflags)
     stream = torch.cuda.Stream()
     b_dev = torch.from_numpy(b_host).cuda()
     x_dev = torch.empty_like(b_dev)
@@ -442,6 +556,11 @@ def main():
                 if peak_kind == 'measured' else 'fallback'}
 
     serve = serve_bench(ctx, args.serve_requests, sq) if args.serve_requests > 0 else None
+    extra_i16 = extra_batch = None
+    if not args.no_extra:
+        ctx.gauge_free(gid)
+        extra_i16 = i16_workload(ctx, sq, stream, args.dslash_iters)
+        extra_batch = batched_workload(ctx, sq, stream)
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -465,6 +584,8 @@ def main():
                        'true_residual': st16['true_residual'], 'long_recon': 12},
             'dslash': dslash,
             'serve': serve,
+            'i16_32x64': extra_i16,
+            'batched_24x64': extra_batch,
             'roofline': roofline,
             'e2e': {'value': round(ms_e2e, 3), 'unit': 'ms', 'h2d_bytes_per_step': h2d,
                     'd2h_bytes_per_step': d2h},

@@ -222,6 +222,31 @@ int cg_solve_multishift(sq_ctx *ctx, int gauge_id, const double *src, int nshift
                         const double *masses, double tol, const sq_cg_opts *opts,
                         double *x, sq_cg_stats *stats);
 
+/* Solve M x = b on the whole lattice, M = m + D on both parities (D as
+ * above).  Staggered D only joins sites of opposite parity, so M x = b splits
+ * into the even-site system of cg_solve and a direct odd-site step:
+ *   (m^2 - D_eo D_oe) x_e = m b_e - D_eo b_o     (CG as in cg_solve, with opts),
+ *   x_o = (b_o - D_oe x_e) / m.
+ * For the even residual r_e of that system, b - M x = (r_e / m, 0), so the
+ * even system is solved to tol * m |b| / |m b_e - D_eo b_o|, which makes
+ * |b - M x| / |b| <= tol.  stats->true_residual is that full-lattice FP64
+ * residual, recomputed on the device from x after the solve (iterations and
+ * reliable updates are the even solve's).  src/x: full-lattice vectors
+ * [site_lex][colour] complex128 (3 V complex), host pointers unless
+ * SQ_CG_DEVICE_PTRS; with SQ_CG_INITIAL_GUESS the even sites of x start the
+ * CG.  Device scratch for the call is taken from the HBM budget and released
+ * on return.  This is the staggered equation the paper's CG inverter solves
+ * (Sec. 2, Fig. 1). */
+int cg_solve_full(sq_ctx *ctx, int gauge_id, const double *src, double mass, double tol,
+                  const sq_cg_opts *opts, double *x, sq_cg_stats *stats);
+
+/* out = (m + D) in on the whole lattice, in FP64: the staggered operator
+ * without even-odd preconditioning.  in_dev/out_dev: distinct device
+ * full-lattice vectors [site_lex][colour] complex128.  Uses device scratch
+ * for the call (HBM budget) and returns once out is written. */
+int dirac_apply(sq_ctx *ctx, int gauge_id, double mass, const double *in_dev, double *out_dev,
+                void *stream);
+
 /* ---- serving -------------------------------------------------------------- */
 
 /* Continuous-batching request loop.  serve_submit copies the host source and

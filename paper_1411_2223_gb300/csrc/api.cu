@@ -209,6 +209,9 @@ extern "C" int gauge_load(sq_ctx *ctx, const int dims[4], const double *fat, con
   g.stride = (g.vh + 63) / 64 * 64;
   g.nchunks = (g.vh + CHUNK - 1) / CHUNK;
   g.t_antiperiodic = (flags & SQ_GAUGE_ANTIPERIODIC_T) ? 1 : 0;
+  geom_set_divisor(g, 0, (uint32_t)g.lxh);
+  geom_set_divisor(g, 1, (uint32_t)dims[1]);
+  geom_set_divisor(g, 2, (uint32_t)dims[2]);
 
   const size_t nlink_bytes = (size_t)vol * 4 * 9 * 16;
   const double *dfat = fat, *dlng = lng;

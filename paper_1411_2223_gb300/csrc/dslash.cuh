@@ -134,6 +134,126 @@ __device__ __forceinline__ void mat_vec_sub(Vec3<R> &acc, const Mat3<R> &m, cons
   }
 }
 
+// ------------------------------------------------------------ 16-bit body
+// 16-bit links stay in their packed words until the mat-vec that uses them
+// (half the registers of decoded floats), which leaves room to load the words
+// of direction mu+1 while direction mu is computed: every thread keeps one
+// direction of links in flight through its whole life instead of waiting for
+// each direction in turn.  Every hop's sign (eta, backward hop, antiperiodic
+// wrap) and scale (link code scale, neighbour norm) is folded into one factor
+// applied to the neighbour vector, so all 16 products accumulate directly.
+
+template <int RECON> struct I16Words {
+  static constexpr int NL = (RECON == 18) ? 18 : 12;
+  uint32_t w[18 + NL];  // fat pair (9 + 9 words), long pair (9 + 9, or 6 + 6)
+};
+
+__device__ __forceinline__ void put4(uint32_t *w, uint4 q) {
+  w[0] = q.x; w[1] = q.y; w[2] = q.z; w[3] = q.w;
+}
+
+template <int RECON>
+__device__ __forceinline__ void i16_load_words(const char *links, int S, int i, int mu,
+                                               I16Words<RECON> &d) {
+  using LL = LinkLayout<PREC_I16, RECON>;
+  const char *fat = links + (size_t)mu * LL::mu_bytes * S;
+  const char *lng = fat + (size_t)LL::fat_bytes * S;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) put4(d.w + 4 * k, ld_stream_u4(fat + ((size_t)k * S + i) * 16));
+  {
+    uint2 q = ld_stream_u2(fat + (size_t)64 * S + (size_t)i * 8);
+    d.w[16] = q.x; d.w[17] = q.y;
+  }
+  if constexpr (RECON == 18) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      put4(d.w + 18 + 4 * k, ld_stream_u4(lng + ((size_t)k * S + i) * 16));
+    uint2 q = ld_stream_u2(lng + (size_t)64 * S + (size_t)i * 8);
+    d.w[34] = q.x; d.w[35] = q.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      put4(d.w + 18 + 4 * k, ld_stream_u4(lng + ((size_t)k * S + i) * 16));
+  }
+}
+
+// acc += M v, M given as 9 code words (row-major)
+__device__ __forceinline__ void mat_vec_words(Vec3<float> &acc, const uint32_t *w,
+                                              const Vec3<float> &v) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2 m = decode_word(w[3 * r + c]);
+      acc.c[r].x = fma(m.x, v.c[c].x, acc.c[r].x);
+      acc.c[r].x = fma(-m.y, v.c[c].y, acc.c[r].x);
+      acc.c[r].y = fma(m.x, v.c[c].y, acc.c[r].y);
+      acc.c[r].y = fma(m.y, v.c[c].x, acc.c[r].y);
+    }
+  }
+}
+
+// Neighbour colour vector in code units times (site norm / 32767) * f.
+__device__ __forceinline__ Vec3<float> i16_vector(const uint4 q, float f) {
+  const float s = __uint_as_float(q.w) * (1.f / 32767.f) * f;
+  Vec3<float> v;
+  v.c[0] = decode_word(q.x);
+  v.c[1] = decode_word(q.y);
+  v.c[2] = decode_word(q.z);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) { v.c[c].x *= s; v.c[c].y *= s; }
+  return v;
+}
+
+template <int RECON, int NR>
+__device__ __forceinline__ void i16_hops(const DslashArgs &a, const SiteCoords &sc, int i, int r0,
+                                         const bool (&active)[NR], Vec3<float> (&acc)[NR]) {
+  const Geom &g = a.g;
+  const int S = g.stride;
+  I16Words<RECON> buf[2];
+  i16_load_words<RECON>(a.links, S, i, 0, buf[0]);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    if (mu < 3) i16_load_words<RECON>(a.links, S, i, mu + 1, buf[(mu + 1) & 1]);
+    const uint32_t *w = buf[mu & 1].w;
+    int nb[4];
+    float f[4];
+    nb[0] = hop<+1>(g, sc, mu, f[0]);
+    nb[1] = hop<-1>(g, sc, mu, f[1]);
+    nb[2] = hop<+3>(g, sc, mu, f[2]);
+    nb[3] = hop<-3>(g, sc, mu, f[3]);
+    const float eta = eta_sign(sc, mu);
+    const float kf = eta * a.ls.fat_k, kl = eta * a.ls.long_k;
+    f[0] *= kf;
+    f[1] *= -kf;
+    f[2] *= kl;
+    f[3] *= -kl;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (!active[r]) continue;
+      const uint4 *in = reinterpret_cast<const uint4 *>(a.in + (size_t)(r0 + r) * a.in_fb);
+      uint4 q[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) q[h] = __ldg(in + nb[h]);
+      mat_vec_words(acc[r], w, i16_vector(q[0], f[0]));
+      mat_vec_words(acc[r], w + 9, i16_vector(q[1], f[1]));
+      if constexpr (RECON == 18) {
+        mat_vec_words(acc[r], w + 18, i16_vector(q[2], f[2]));
+        mat_vec_words(acc[r], w + 27, i16_vector(q[3], f[3]));
+      } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          Mat3<float> m;
+#pragma unroll
+          for (int e = 0; e < 6; ++e) m.e[e] = decode_word(w[18 + 6 * h + e]);
+          reconstruct_row2(m, a.ls.recon_f);
+          mat_vec_acc(acc[r], m, i16_vector(q[2 + h], f[2 + h]));
+        }
+      }
+    }
+  }
+}
+
 // Launch bounds per precision: FP64 needs the large register file of the SM
 // (a 512-thread bound squeezes it to 64 registers and spills); FP32 and
 // 16-bit fit 128 registers at up to 512 threads.
@@ -186,43 +306,43 @@ dslash_kernel(const DslashArgs a) {
 
   if (valid) {
     const SiteCoords sc = site_coords(g, a.out_parity, i);
+    if constexpr (PREC == PREC_I16) {
+      i16_hops<RECON, NR>(a, sc, i, r0, active, acc);
+    } else {
 #pragma unroll 1
-    for (int mu = 0; mu < 4; ++mu) {
-      Mat3<R> m[4];
-      LinkIO<PREC, RECON>::load(a.links, S, i, mu, a.ls, m);
-      float sg[4];
-      int nb[4];
-      nb[0] = hop_index(g, sc, mu, +1, sg[0]);
-      nb[1] = hop_index(g, sc, mu, -1, sg[1]);
-      nb[2] = hop_index(g, sc, mu, +3, sg[2]);
-      nb[3] = hop_index(g, sc, mu, -3, sg[3]);
-      if constexpr (PREC == PREC_I16) {
-        sg[0] *= a.ls.fat_k; sg[1] *= a.ls.fat_k;
-        sg[2] *= a.ls.long_k; sg[3] *= a.ls.long_k;
-      }
-      const float eta = eta_sign(sc, mu);
+      for (int mu = 0; mu < 4; ++mu) {
+        Mat3<R> m[4];
+        LinkIO<PREC, RECON>::load(a.links, S, i, mu, a.ls, m);
+        float sg[4];
+        int nb[4];
+        nb[0] = hop_index(g, sc, mu, +1, sg[0]);
+        nb[1] = hop_index(g, sc, mu, -1, sg[1]);
+        nb[2] = hop_index(g, sc, mu, +3, sg[2]);
+        nb[3] = hop_index(g, sc, mu, -3, sg[3]);
+        const float eta = eta_sign(sc, mu);
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if (!active[r]) continue;
-        const char *f = a.in + (size_t)(r0 + r) * a.in_fb;
-        const char *fx = (a.xs != nullptr) ? a.xs + (size_t)(r0 + r) * a.xs_fb : nullptr;
-        Vec3<R> t;
-        zero(t);
-        Vec3<R> v;
-        v = gather_in<PREC, MODE, R>(f, fx, a.xs_prec, S, nb[0], sg[0]);
-        mat_vec_acc(t, m[0], v);
-        v = gather_in<PREC, MODE, R>(f, fx, a.xs_prec, S, nb[1], sg[1]);
-        mat_vec_sub(t, m[1], v);
-        v = gather_in<PREC, MODE, R>(f, fx, a.xs_prec, S, nb[2], sg[2]);
-        mat_vec_acc(t, m[2], v);
-        v = gather_in<PREC, MODE, R>(f, fx, a.xs_prec, S, nb[3], sg[3]);
-        mat_vec_sub(t, m[3], v);
-        if (eta > 0.f) {
+        for (int r = 0; r < NR; ++r) {
+          if (!active[r]) continue;
+          const char *f = a.in + (size_t)(r0 + r) * a.in_fb;
+          const char *fx = (a.xs != nullptr) ? a.xs + (size_t)(r0 + r) * a.xs_fb : nullptr;
+          Vec3<R> t;
+          zero(t);
+          Vec3<R> v;
+          v = gather_in<PREC, MODE, R>(f, fx, a.xs_prec, S, nb[0], sg[0]);
+          mat_vec_acc(t, m[0], v);
+          v = gather_in<PREC, MODE, R>(f, fx, a.xs_prec, S, nb[1], sg[1]);
+          mat_vec_sub(t, m[1], v);
+          v = gather_in<PREC, MODE, R>(f, fx, a.xs_prec, S, nb[2], sg[2]);
+          mat_vec_acc(t, m[2], v);
+          v = gather_in<PREC, MODE, R>(f, fx, a.xs_prec, S, nb[3], sg[3]);
+          mat_vec_sub(t, m[3], v);
+          if (eta > 0.f) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) { acc[r].c[c].x += t.c[c].x; acc[r].c[c].y += t.c[c].y; }
-        } else {
+            for (int c = 0; c < 3; ++c) { acc[r].c[c].x += t.c[c].x; acc[r].c[c].y += t.c[c].y; }
+          } else {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) { acc[r].c[c].x -= t.c[c].x; acc[r].c[c].y -= t.c[c].y; }
+            for (int c = 0; c < 3; ++c) { acc[r].c[c].x -= t.c[c].x; acc[r].c[c].y -= t.c[c].y; }
+          }
         }
       }
     }

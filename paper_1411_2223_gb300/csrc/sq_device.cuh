@@ -20,14 +20,20 @@ struct SiteCoords {
   int lex;
 };
 
+__device__ __forceinline__ uint32_t geom_div(const Geom &g, int k, uint32_t n) {
+  uint32_t t = __umulhi(n, g.div_m[k]);
+  return (t + ((n - t) >> g.div_s1[k])) >> g.div_s2[k];
+}
+
 __device__ __forceinline__ SiteCoords site_coords(const Geom &g, int parity, int i) {
   SiteCoords s;
-  int xh = i % g.lxh;
-  int r = i / g.lxh;
-  s.c[1] = r % g.L[1];
-  r /= g.L[1];
-  s.c[2] = r % g.L[2];
-  s.c[3] = r / g.L[2];
+  uint32_t r = geom_div(g, 0, (uint32_t)i);
+  const int xh = i - (int)r * g.lxh;
+  uint32_t r2 = geom_div(g, 1, r);
+  s.c[1] = (int)(r - r2 * (uint32_t)g.L[1]);
+  uint32_t r3 = geom_div(g, 2, r2);
+  s.c[2] = (int)(r2 - r3 * (uint32_t)g.L[2]);
+  s.c[3] = (int)r3;
   s.c[0] = 2 * xh + ((parity + s.c[1] + s.c[2] + s.c[3]) & 1);
   s.lex = s.c[0] + g.L[0] * (s.c[1] + g.L[1] * (s.c[2] + g.L[2] * s.c[3]));
   return s;
@@ -43,6 +49,26 @@ __device__ __forceinline__ int hop_index(const Geom &g, const SiteCoords &s, int
   while (c < 0) { c += L; ++wraps; }
   while (c >= L) { c -= L; ++wraps; }
   sign = (mu == 3 && g.t_antiperiodic && (wraps & 1)) ? -1.f : 1.f;
+  return (s.lex + (c - s.c[mu]) * g.st[mu]) >> 1;
+}
+
+// Same as hop_index for a hop length D known at compile time (|D| <= 3,
+// L >= 2: at most two wraps, only in the direction of the hop).
+template <int D>
+__device__ __forceinline__ int hop(const Geom &g, const SiteCoords &s, int mu, float &sign) {
+  const int L = g.L[mu];
+  int c = s.c[mu] + D;
+  bool w1, w2 = false;
+  if constexpr (D > 0) {
+    w1 = c >= L;
+    c -= w1 ? L : 0;
+    if constexpr (D > 1) { w2 = c >= L; c -= w2 ? L : 0; }
+  } else {
+    w1 = c < 0;
+    c += w1 ? L : 0;
+    if constexpr (D < -1) { w2 = c < 0; c += w2 ? L : 0; }
+  }
+  sign = (mu == 3 && g.t_antiperiodic && (w1 != w2)) ? -1.f : 1.f;
   return (s.lex + (c - s.c[mu]) * g.st[mu]) >> 1;
 }
 

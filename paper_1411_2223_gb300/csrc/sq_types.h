@@ -17,7 +17,21 @@ struct Geom {
   int stride;          // plane stride in sites (vh rounded up to 64)
   int nchunks;         // ceil(vh / CHUNK)
   int t_antiperiodic;  // 1: hops wrapping around t pick up -1
+  // exact division by Lx/2, Ly, Lz with a multiply-high (Granlund-Montgomery)
+  uint32_t div_m[3];
+  int div_s1[3], div_s2[3];
 };
+
+// Multiplier and shifts for q = n / d with q = (t + ((n - t) >> s1)) >> s2,
+// t = umulhi(n, m): exact for every 32-bit n (Granlund and Montgomery, "Division
+// by invariant integers using multiplication", PLDI 1994, Sec. 4).
+inline void geom_set_divisor(Geom &g, int k, uint32_t d) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  g.div_m[k] = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  g.div_s1[k] = l > 0 ? 1 : 0;
+  g.div_s2[k] = l > 0 ? l - 1 : 0;
+}
 
 // Bytes of one packed parity-half colour vector.
 inline size_t spinor_bytes(int prec, int stride) {

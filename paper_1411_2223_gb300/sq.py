@@ -93,6 +93,9 @@ SIGNATURES = {
                             ctypes.POINTER(CgStats)]),
     'cg_solve_multishift': (_I, [_P, _I, _P, _I, _P, _D, ctypes.POINTER(CgOpts), _P,
                                  ctypes.POINTER(CgStats)]),
+    'cg_solve_full': (_I, [_P, _I, _P, _D, _D, ctypes.POINTER(CgOpts), _P,
+                           ctypes.POINTER(CgStats)]),
+    'dirac_apply': (_I, [_P, _I, _D, _P, _P, _P]),
     'serve_submit': (_I, [_P, _I, _P, _D, _D, ctypes.POINTER(_U64)]),
     'serve_poll': (_I, [_P, _U64, _P, ctypes.POINTER(CgStats), _I]),
     'serve_cancel': (_I, [_P, _U64]),
@@ -329,6 +332,43 @@ class Context:
             _check(status, 'cg_solve_multishift')
         return x, [st.as_dict() for st in stats], status
 
+    def cg_solve_full(self, gauge_id, src, mass, tol, precision='f32', long_recon=18,
+                      delta=-1.0, max_iter=100000, block_iters=16, x0=None, graph=True,
+                      stream=None, check=True):
+        """Solve (m + D) x = src on the whole lattice.  Returns (x, stats dict).
+
+        src: numpy (V, 3) complex128 in site_lex order (host) or a torch
+        complex128 CUDA tensor (x is then a device tensor).
+        """
+        dev = _is_device(src)
+        if dev:
+            s = src.contiguous()
+            x = s.new_zeros(s.shape)
+        else:
+            s = np.ascontiguousarray(src, dtype=np.complex128)
+            x = np.zeros_like(s)
+        flags = CG_DEVICE_PTRS if dev else 0
+        if x0 is not None:
+            flags |= CG_INITIAL_GUESS
+            if dev:
+                x.copy_(x0)
+            else:
+                x[...] = np.asarray(x0)
+        if not graph:
+            flags |= CG_NO_GRAPH
+        o = self._opts(precision, long_recon, delta, max_iter, block_iters, flags, stream)
+        st = CgStats()
+        status = self._lib.cg_solve_full(self.handle, gauge_id, _ptr(s), float(mass), float(tol),
+                                         ctypes.byref(o), _ptr(x), ctypes.byref(st))
+        if check:
+            _check(status, 'cg_solve_full')
+        return x, st.as_dict()
+
+    def dirac_apply(self, gauge_id, mass, in_dev, out_dev, stream=None):
+        """out = (m + D) in on the whole lattice, FP64, device (V, 3) complex128."""
+        _check(self._lib.dirac_apply(self.handle, gauge_id, float(mass), _ptr(in_dev),
+                                     _ptr(out_dev), _stream(stream)), 'dirac_apply')
+
     # --------------------------------------------------------------- serving
     def serve_configure(self, slots_per_batch=8, block_iters=8):
         _check(self._lib.serve_configure(self.handle, int(slots_per_batch), int(block_iters)),
@@ -368,6 +408,7 @@ def _forward(name):
 
 
 for _n in ('gauge_load', 'gauge_free', 'dslash_apply', 'mdagm_apply', 'cg_solve',
-           'cg_solve_multi', 'cg_solve_multishift', 'serve_submit', 'serve_poll',
+           'cg_solve_multi', 'cg_solve_multishift', 'cg_solve_full', 'dirac_apply',
+           'serve_submit', 'serve_poll',
            'serve_cancel', 'serve_stats', 'serve_configure'):
     globals()[_n] = _forward(_n)

@@ -182,3 +182,29 @@ def test_config2_full_size_20x64(sq, prec, recon):
         assert r <= 1e-8, r
     finally:
         sq.gauge_free(gid)
+
+
+def test_config3_full_size_32x64_i16(sq):
+    """32^3 x 64, eps 0.25, am 0.01, tol 1e-8: 16-bit storage with per-site
+    norms and 12-real long links, FP32 accumulation, FP64 reliable updates --
+    the 16-bit workload at its full size, in the launch configuration the
+    benchmark times.  The oracle recomputes the FP64 residual of the result,
+    and the 16-bit Dslash at this size is checked against the oracle."""
+    from paper_1411_2223_gb300 import sq as sqm
+    from gpu_helpers import TOL_DSLASH, gpu_dslash, rel
+    dims = (32, 32, 32, 64)
+    fat, lng = synth.gauge_field(dims, 0.25, 0)
+    vh = oracle.volume(dims) // 2
+    b = synth.gaussian_source(vh, 0)
+    gid = sq.gauge_load(dims, fat, lng, flags=sqm.GAUGE_NO_F32)
+    try:
+        x, st = sq.cg_solve(gid, b, 0.01, 1e-8, precision='i16', long_recon=12)
+        assert st['status'] == 0
+        r = oracle.true_residual(dims, fat, lng, 0.01, b, x)
+        assert r <= 1e-8, r
+        assert abs(r - st['true_residual']) <= 1e-3 * r
+        want = oracle.dslash_half(dims, fat, lng, b, 1)
+        got = gpu_dslash(sq, gid, 'i16', 12, b, 1, vh)
+        assert rel(got, want) <= TOL_DSLASH['i16']
+    finally:
+        sq.gauge_free(gid)

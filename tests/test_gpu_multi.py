@@ -112,3 +112,32 @@ def test_multishift_device_pointers(sq):
             assert oracle.true_residual(dims, fat, lng, m, b, xh[i]) <= 1e-8
     finally:
         sq.gauge_free(gid)
+
+
+def test_batched_full_size_24x64(sq):
+    """24^3 x 64, eps 0.25, tol 1e-8: 12 sources (seeds 0..11) at am 0.01 in
+    one batched solve, and 8 masses am = 0.005 * 20^(i/7) in one multi-shift
+    solve -- the batched workload at full size.  The oracle recomputes the FP64
+    residual of every multi-shift solution and of four sampled batch members;
+    the rest are checked through the library's FP64 residual."""
+    from paper_1411_2223_gb300 import sq as sqm
+    dims = (24, 24, 24, 64)
+    fat, lng = synth.gauge_field(dims, 0.25, 0)
+    vh = oracle.volume(dims) // 2
+    srcs = synth.gaussian_sources(vh, range(12))
+    tol = 1e-8
+    gid = sq.gauge_load(dims, fat, lng, flags=sqm.GAUGE_NO_I16 | sqm.GAUGE_NO_LONG12)
+    try:
+        xs, stats, status = sq.cg_solve_multi(gid, srcs, [0.01] * 12, tol)
+        assert status == 0
+        assert all(s['status'] == 0 and s['true_residual'] <= tol for s in stats)
+        for j in (0, 5, 7, 11):
+            assert oracle.true_residual(dims, fat, lng, 0.01, srcs[j], xs[j]) <= tol
+        masses = 0.005 * 20.0 ** (np.arange(8) / 7.0)
+        xm, sm, status = sq.cg_solve_multishift(gid, srcs[0], masses, tol)
+        assert status == 0
+        for i, m in enumerate(masses):
+            assert sm[i]['status'] == 0
+            assert oracle.true_residual(dims, fat, lng, m, srcs[0], xm[i]) <= tol
+    finally:
+        sq.gauge_free(gid)
