@@ -329,6 +329,62 @@ def i16_workload(ctx, sq, stream, dslash_iters):
             'fp64_error_vs_fp64_cg': err, 'dslash': dsl}
 
 
+def fp64_peak_tflops():
+    """Measured FP64 throughput of this GPU (cuBLAS DGEMM through torch, best
+    of 3): the denominator of the FP64-bound kernels' rooflines."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device='cuda')
+    b = torch.randn(n, n, dtype=torch.float64, device='cuda')
+    torch.matmul(a, b)
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def full_lattice_workload(ctx, sq, stream, fat, lng):
+    """The whole-lattice solve (m + D) x = b at 20^3 x 64 and the GPU link
+    fattening of the same lattice's thin links."""
+    import numpy as np
+    import torch
+    import synth
+    dims = DIMS
+    vol = int(np.prod(dims))
+    gid = ctx.gauge_load(dims, fat, lng, flags=sq.GAUGE_NO_I16 | sq.GAUGE_NO_LONG12)
+    g = np.random.default_rng(SRC_SEED).standard_normal((vol, 3, 2))
+    b = torch.from_numpy(g[..., 0] + 1j * g[..., 1]).cuda()
+    ctx.cg_solve_full(gid, b, MASS, TOL, stream=stream)
+    ms, (x, st) = timed(lambda: ctx.cg_solve_full(gid, b, MASS, TOL, stream=stream), stream, 2)
+    ctx.gauge_free(gid)
+    thin = torch.from_numpy(synth.thin_links(dims, EPS, GAUGE_SEED)).cuda()
+    f, l = torch.empty_like(thin), torch.empty_like(thin)
+    ctx.gauge_fatten(dims, thin, f, l, stream=stream)
+    ms_f, _ = timed(lambda: ctx.gauge_fatten(dims, thin, f, l, stream=stream), stream, 5)
+    # flops per link: 6 staples x 2 products + Naik 2 products, 3x3 complex
+    # product = 27 complex multiply-adds = 216 real flops; plus the sums
+    flops = 4 * vol * (14 * 216 + 6 * 18 + 36)
+    peak = fp64_peak_tflops()
+    gfl = flops / (ms_f * 1e-3) / 1e9
+    return {'solve': {'workload': '20^3x64 whole lattice (m + D) x = b, Gaussian source (seed 0), '
+                                  'am 0.01, tol 1e-8: even-site FP32 CG + FP64 reliable updates, '
+                                  'odd sites reconstructed',
+                      'ms': round(ms, 3), 'iterations': st['iterations'],
+                      'full_true_residual': st['true_residual']},
+            'fatten': {'workload': '20^3x64 thin links (eps 0.25, seed 0) -> fat (6 staples) and '
+                                   'long links, FP64',
+                       'ms': round(ms_f, 3), 'gflops_fp64': round(gfl, 1),
+                       'roofline': {'bound': 'alu', 'achieved': round(gfl / 1e3, 4),
+                                    'peak': round(peak, 4), 'unit': 'TFLOP/s',
+                                    'frac': round(gfl / 1e3 / peak, 4),
+                                    'peak_kind': 'measured FP64 DGEMM (torch.matmul 4096^3)'}}}
+
+
 def batched_workload(ctx, sq, stream):
     """24^3 x 64: 12 right-hand sides in one batched solve against 12 single
     solves, and 8 masses in one multi-shift solve against 8 single solves."""
@@ -556,9 +612,10 @@ def main():
                 if peak_kind == 'measured' else 'fallback'}
 
     serve = serve_bench(ctx, args.serve_requests, sq) if args.serve_requests > 0 else None
-    extra_i16 = extra_batch = None
+    extra_i16 = extra_batch = extra_full = None
     if not args.no_extra:
         ctx.gauge_free(gid)
+        extra_full = full_lattice_workload(ctx, sq, stream, fat, lng)
         extra_i16 = i16_workload(ctx, sq, stream, args.dslash_iters)
         extra_batch = batched_workload(ctx, sq, stream)
 
@@ -586,6 +643,7 @@ def main():
             'serve': serve,
             'i16_32x64': extra_i16,
             'batched_24x64': extra_batch,
+            'whole_lattice_20x64': extra_full,
             'roofline': roofline,
             'e2e': {'value': round(ms_e2e, 3), 'unit': 'ms', 'h2d_bytes_per_step': h2d,
                     'd2h_bytes_per_step': d2h},

@@ -145,6 +145,25 @@ int gauge_load(sq_ctx *ctx, const int dims[4], const double *fat, const double *
                unsigned flags, int *gauge_id);
 int gauge_free(sq_ctx *ctx, int gauge_id);
 
+/* Fat and long links from thin links, on the device in FP64:
+ *   F_mu(x) = c1 [ U_mu(x) + w sum_{nu != mu} ( U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
+ *              + U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) ) ] / (1 + 6w),
+ *   L_mu(x) = c3 U_mu(x) U_mu(x+mu) U_mu(x+2mu),
+ * with periodic neighbours (w = staple_weight; the benchmark workloads use
+ * c1 = 9/8, c3 = -1/24, w = 0.1).  This stands in for the asqtad link
+ * fattening that produces the paper's MILC links (Sec. 2, Fig. 1); it is not
+ * MILC's full path set.  thin_dev, fat_dev, lng_dev: distinct device arrays
+ * in the links layout above.  Asynchronous on `stream`. */
+int gauge_fatten(sq_ctx *ctx, const int dims[4], const double *thin_dev, double c1, double c3,
+                 double staple_weight, double *fat_dev, double *lng_dev, void *stream);
+
+/* gauge_fatten followed by gauge_load: thin links in (host pointer, or device
+ * with SQ_GAUGE_DEVICE_PTRS), a gauge id out.  The fat and long links exist
+ * on the device only transiently (staging outside the HBM budget, freed on
+ * return).  Other flags as for gauge_load. */
+int gauge_load_thin(sq_ctx *ctx, const int dims[4], const double *thin, double c1, double c3,
+                    double staple_weight, unsigned flags, int *gauge_id);
+
 /* Bytes of one packed parity-half vector of `prec` for this gauge field's
  * lattice, and the plane stride in sites. */
 int sq_spinor_bytes(sq_ctx *ctx, int gauge_id, int prec, size_t *bytes, int *stride);

@@ -68,6 +68,7 @@ def _load():
             lib.oracle_parity.restype = I
             lib.oracle_quantize_spinor_i16.argtypes = [Lg, P, P, P]
             lib.oracle_quantize_links_i16.argtypes = [Lg, P, D, P]
+            lib.oracle_fat_long.argtypes = [P, P, D, D, D, P, P]
             _lib = lib
     return _lib
 
@@ -188,6 +189,24 @@ def cg(dims, fat, lng, mass, b_even, tol, max_iter=100000, t_sign=1):
     it = lib.oracle_cg(_ptr(_dims(dims)), _ptr(fat), _ptr(lng), int(t_sign), float(mass),
                        _ptr(b), float(tol), int(max_iter), _ptr(x), ctypes.byref(tr))
     return extract_half(dims, 0, x), it, tr.value
+
+
+C1 = 9.0 / 8.0
+C3 = -1.0 / 24.0
+STAPLE_WEIGHT = 0.1
+
+
+def fat_long(dims, thin, c1=C1, c3=C3, w=STAPLE_WEIGHT):
+    """Fat and long links (V, 4, 3, 3) from thin links by the workloads'
+    recipe: F = c1 [U + w * (6 staples)] / (1 + 6w), L = c3 U U U (see
+    oracle.c; the paper's links are MILC asqtad links, Sec. 2)."""
+    lib = _load()
+    u = _c128(thin)
+    fat = np.zeros_like(u)
+    lng = np.zeros_like(u)
+    lib.oracle_fat_long(_ptr(_dims(dims)), _ptr(u), float(c1), float(c3), float(w), _ptr(fat),
+                        _ptr(lng))
+    return fat, lng
 
 
 def dirac(dims, fat, lng, mass, v, t_sign=1):

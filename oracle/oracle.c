@@ -441,3 +441,62 @@ void oracle_quantize_links_i16(long n, const double *v, double scale, short *q)
         q[k] = (short)r;
     }
 }
+
+/* ------------------------------------------------------ fat and long links
+ * The benchmark workloads' link recipe (the paper's lattices are MILC asqtad
+ * ensembles, Sec. 2 and Fig. 1, which are not available here), applied to
+ * thin links U:
+ *   F_mu(x) = c1 [ U_mu(x) + w sum_{nu != mu} ( U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
+ *                + U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) ) ] / (1 + 6w),
+ *   L_mu(x) = c3 U_mu(x) U_mu(x+mu) U_mu(x+2mu).
+ * Every neighbour is periodic; links carry no boundary sign. */
+
+/* c = a b, a^dag b or a b^dag (3x3, row-major) */
+static void mat_mul(cplx *c, const cplx *a, const cplx *b, int dag_a, int dag_b)
+{
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            cplx t = 0;
+            for (int k = 0; k < 3; k++) {
+                cplx x = dag_a ? conj(a[3 * k + i]) : a[3 * i + k];
+                cplx y = dag_b ? conj(b[3 * j + k]) : b[3 * k + j];
+                t += x * y;
+            }
+            c[3 * i + j] = t;
+        }
+}
+
+void oracle_fat_long(const int L[4], const double *u, double c1, double c3, double w,
+                     double *fat, double *lng)
+{
+    long vol = oracle_volume(L);
+    #pragma omp parallel for schedule(static)
+    for (long s = 0; s < vol; s++) {
+        for (int mu = 0; mu < 4; mu++) {
+            const cplx *umu = link_at(u, s, mu);
+            long xpm = oracle_neighbor(L, s, mu, 1, 1, NULL);
+            cplx staples[9] = {0}, t[9], t2[9];
+            for (int nu = 0; nu < 4; nu++) {
+                if (nu == mu) continue;
+                /* up: U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag */
+                long xpn = oracle_neighbor(L, s, nu, 1, 1, NULL);
+                mat_mul(t, link_at(u, s, nu), link_at(u, xpn, mu), 0, 0);
+                mat_mul(t2, t, link_at(u, xpm, nu), 0, 1);
+                for (int e = 0; e < 9; e++) staples[e] += t2[e];
+                /* down: U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) */
+                long xmn = oracle_neighbor(L, s, nu, -1, 1, NULL);
+                long xmnpm = oracle_neighbor(L, xmn, mu, 1, 1, NULL);
+                mat_mul(t, link_at(u, xmn, nu), link_at(u, xmn, mu), 1, 0);
+                mat_mul(t2, t, link_at(u, xmnpm, nu), 0, 0);
+                for (int e = 0; e < 9; e++) staples[e] += t2[e];
+            }
+            cplx *f = (cplx *)(fat + ((s * 4 + mu) * 9) * 2);
+            for (int e = 0; e < 9; e++) f[e] = c1 * (umu[e] + w * staples[e]) / (1.0 + 6.0 * w);
+            long xp2m = oracle_neighbor(L, s, mu, 2, 1, NULL);
+            mat_mul(t, umu, link_at(u, xpm, mu), 0, 0);
+            mat_mul(t2, t, link_at(u, xp2m, mu), 0, 0);
+            cplx *l = (cplx *)(lng + ((s * 4 + mu) * 9) * 2);
+            for (int e = 0; e < 9; e++) l[e] = c3 * t2[e];
+        }
+    }
+}

@@ -158,22 +158,23 @@ __device__ __forceinline__ void i16_load_words(const char *links, int S, int i, 
   using LL = LinkLayout<PREC_I16, RECON>;
   const char *fat = links + (size_t)mu * LL::mu_bytes * S;
   const char *lng = fat + (size_t)LL::fat_bytes * S;
+  const uint64_t pol = l2_evict_first_policy();
 #pragma unroll
-  for (int k = 0; k < 4; ++k) put4(d.w + 4 * k, ld_stream_u4(fat + ((size_t)k * S + i) * 16));
+  for (int k = 0; k < 4; ++k) put4(d.w + 4 * k, ld_stream_u4(fat + ((size_t)k * S + i) * 16, pol));
   {
-    uint2 q = ld_stream_u2(fat + (size_t)64 * S + (size_t)i * 8);
+    uint2 q = ld_stream_u2(fat + (size_t)64 * S + (size_t)i * 8, pol);
     d.w[16] = q.x; d.w[17] = q.y;
   }
   if constexpr (RECON == 18) {
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      put4(d.w + 18 + 4 * k, ld_stream_u4(lng + ((size_t)k * S + i) * 16));
-    uint2 q = ld_stream_u2(lng + (size_t)64 * S + (size_t)i * 8);
+      put4(d.w + 18 + 4 * k, ld_stream_u4(lng + ((size_t)k * S + i) * 16, pol));
+    uint2 q = ld_stream_u2(lng + (size_t)64 * S + (size_t)i * 8, pol);
     d.w[34] = q.x; d.w[35] = q.y;
   } else {
 #pragma unroll
     for (int k = 0; k < 3; ++k)
-      put4(d.w + 18 + 4 * k, ld_stream_u4(lng + ((size_t)k * S + i) * 16));
+      put4(d.w + 18 + 4 * k, ld_stream_u4(lng + ((size_t)k * S + i) * 16, pol));
   }
 }
 
@@ -254,6 +255,49 @@ __device__ __forceinline__ void i16_hops(const DslashArgs &a, const SiteCoords &
   }
 }
 
+// ------------------------------------------------------ many right-hand sides
+// With NR >= 8 systems per thread the link stream is no longer the cost (each
+// link is read once for all of them); registers are.  One pair of hop
+// matrices is held at a time and applied to every system, with the hop's
+// sign (eta, backward hop, antiperiodic wrap) folded into the gathered vector.
+template <int RECON, int NR>
+__device__ __forceinline__ void many_rhs_hops(const DslashArgs &a, const SiteCoords &sc, int i,
+                                              int r0, const bool (&active)[NR],
+                                              Vec3<float> (&acc)[NR]) {
+  const Geom &g = a.g;
+  const int S = g.stride;
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+    int nb[4];
+    float f[4];
+    nb[0] = hop<+1>(g, sc, mu, f[0]);
+    nb[1] = hop<-1>(g, sc, mu, f[1]);
+    nb[2] = hop<+3>(g, sc, mu, f[2]);
+    nb[3] = hop<-3>(g, sc, mu, f[3]);
+    const float eta = eta_sign(sc, mu);
+    f[0] *= eta;
+    f[1] *= -eta;
+    f[2] *= eta;
+    f[3] *= -eta;
+#pragma unroll
+    for (int kind = 0; kind < 2; ++kind) {
+      Mat3<float> m[2];
+      if (kind == 0) LinkIO<PREC_F32, RECON>::template load_pair<0>(a.links, S, i, mu, a.ls, m);
+      else LinkIO<PREC_F32, RECON>::template load_pair<1>(a.links, S, i, mu, a.ls, m);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (!active[r]) continue;
+        const char *in = a.in + (size_t)(r0 + r) * a.in_fb;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const Vec3<float> v = gather<PREC_F32, float>(in, S, nb[2 * kind + h], f[2 * kind + h]);
+          mat_vec_acc(acc[r], m[h], v);
+        }
+      }
+    }
+  }
+}
+
 // Launch bounds per precision: FP64 needs the large register file of the SM
 // (a 512-thread bound squeezes it to 64 registers and spills); FP32 and
 // 16-bit fit 128 registers at up to 512 threads.
@@ -295,8 +339,9 @@ dslash_kernel(const DslashArgs a) {
 
   // the epilogue's own-site operand is fetched up front so its latency hides
   // behind the link stream
-  Vec3<R> pre[NR];
-  if constexpr (MODE == MODE_MDAGM) {
+  constexpr bool kPreP = (MODE == MODE_MDAGM) && NR < 8;  // registers allow it
+  Vec3<R> pre[kPreP ? NR : 1];
+  if constexpr (kPreP) {
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       if (valid && active[r]) pre[r] = SpinorIO<PREC>::load(a.p + (size_t)(r0 + r) * a.p_fb, S, i);
@@ -308,6 +353,8 @@ dslash_kernel(const DslashArgs a) {
     const SiteCoords sc = site_coords(g, a.out_parity, i);
     if constexpr (PREC == PREC_I16) {
       i16_hops<RECON, NR>(a, sc, i, r0, active, acc);
+    } else if constexpr (PREC == PREC_F32 && NR >= 8) {
+      many_rhs_hops<RECON, NR>(a, sc, i, r0, active, acc);
     } else {
 #pragma unroll 1
       for (int mu = 0; mu < 4; ++mu) {
@@ -367,7 +414,9 @@ dslash_kernel(const DslashArgs a) {
       dot[r] = 0.0;
       if (valid && active[r]) {
         const R m2 = (R)(a.slots ? a.slots[r0 + r].m2 : a.m2_const);
-        const Vec3<R> &p = pre[r];
+        Vec3<R> p;
+        if constexpr (kPreP) p = pre[r];
+        else p = SpinorIO<PREC>::load(a.p + (size_t)(r0 + r) * a.p_fb, S, i);
         Vec3<R> o;
         R d = 0;
 #pragma unroll

@@ -11,7 +11,8 @@ int launch_dslash_f32(int recon, int nr, int mode, int outp, const DslashArgs &a
     dslash_kernel<PREC_F32, RC, NR, MODE, OUTP><<<grid, block, 0, st>>>(a); \
     return 0; \
   }
-#define SQ_K_NR(RC, MODE, OUTP) SQ_K(RC, 1, MODE, OUTP) SQ_K(RC, 2, MODE, OUTP) SQ_K(RC, 4, MODE, OUTP)
+#define SQ_K_NR(RC, MODE, OUTP) SQ_K(RC, 1, MODE, OUTP) SQ_K(RC, 2, MODE, OUTP) SQ_K(RC, 4, MODE, OUTP) \
+  SQ_K(RC, 8, MODE, OUTP) SQ_K(RC, 12, MODE, OUTP)
   SQ_K_NR(18, MODE_PLAIN, PREC_F32)
   SQ_K_NR(12, MODE_PLAIN, PREC_F32)
   SQ_K_NR(18, MODE_MDAGM, PREC_F32)

@@ -127,31 +127,40 @@ __device__ __forceinline__ void reconstruct_row2(Mat3<R> &m, R f) {
 }
 
 // ------------------------------------------------------- read-only loads
-// Links stream from HBM once per Dslash: keep them out of L1.  Colour
-// vectors are gathered 16 times per site: let them allocate in L1.
+// Links stream from HBM once per Dslash: keep them out of L1, and mark them
+// evict-first in L2 so that the stream does not push out the colour vectors
+// every kernel of a CG iteration reads again (a few MB per field, resident
+// in L2).  Colour vectors are gathered 16 times per site: let them allocate
+// in L1.
 
-__device__ __forceinline__ float4 ld_stream_f4(const void *p) {
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ float4 ld_stream_f4(const void *p, uint64_t pol) {
   float4 v;
-  asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
   return v;
 }
-__device__ __forceinline__ double2 ld_stream_d2(const void *p) {
+__device__ __forceinline__ double2 ld_stream_d2(const void *p, uint64_t pol) {
   double2 v;
-  asm("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];"
-               : "=d"(v.x), "=d"(v.y) : "l"(p));
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
+      : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
   return v;
 }
-__device__ __forceinline__ uint4 ld_stream_u4(const void *p) {
+__device__ __forceinline__ uint4 ld_stream_u4(const void *p, uint64_t pol) {
   uint4 v;
-  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(pol));
   return v;
 }
-__device__ __forceinline__ uint2 ld_stream_u2(const void *p) {
+__device__ __forceinline__ uint2 ld_stream_u2(const void *p, uint64_t pol) {
   uint2 v;
-  asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];"
-               : "=r"(v.x), "=r"(v.y) : "l"(p));
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+      : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
   return v;
 }
 
@@ -315,16 +324,17 @@ template <int RECON> struct LinkIO<PREC_F64, RECON> {
                                               const LinkScales &ls, Mat3<double> m[4]) {
     const char *fat = links + (size_t)mu * LL::mu_bytes * S;
     const char *lng = fat + (size_t)LL::fat_bytes * S;
+    const uint64_t pol = l2_evict_first_policy();
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      m[0].e[k] = ld_stream_d2(fat + ((size_t)k * S + i) * 16);
-      m[1].e[k] = ld_stream_d2(fat + ((size_t)(9 + k) * S + i) * 16);
+      m[0].e[k] = ld_stream_d2(fat + ((size_t)k * S + i) * 16, pol);
+      m[1].e[k] = ld_stream_d2(fat + ((size_t)(9 + k) * S + i) * 16, pol);
     }
     constexpr int n = (RECON == 18) ? 9 : 6;
 #pragma unroll
     for (int k = 0; k < n; ++k) {
-      m[2].e[k] = ld_stream_d2(lng + ((size_t)k * S + i) * 16);
-      m[3].e[k] = ld_stream_d2(lng + ((size_t)(n + k) * S + i) * 16);
+      m[2].e[k] = ld_stream_d2(lng + ((size_t)k * S + i) * 16, pol);
+      m[3].e[k] = ld_stream_d2(lng + ((size_t)(n + k) * S + i) * 16, pol);
     }
     if (RECON == 12) {
       reconstruct_row2(m[2], ls.recon_d);
@@ -342,13 +352,42 @@ __device__ __forceinline__ void f4_to_mats(const float4 *q, int nq, float *dst) 
 
 template <int RECON> struct LinkIO<PREC_F32, RECON> {
   using LL = LinkLayout<PREC_F32, RECON>;
+  // One pair of direction mu: the fat pair (F_mu(x), F_mu(x-mu)^dag) for
+  // kind 0, the long pair (L_mu(x), L_mu(x-3mu)^dag) for kind 1.
+  template <int KIND>
+  static __device__ __forceinline__ void load_pair(const char *links, int S, int i, int mu,
+                                                   const LinkScales &ls, Mat3<float> m[2]) {
+    const char *base = links + (size_t)mu * LL::mu_bytes * S;
+    if (KIND == 1) base += (size_t)LL::fat_bytes * S;
+    const uint64_t pol = l2_evict_first_policy();
+    constexpr int nq = (KIND == 0 || RECON == 18) ? 9 : 6;
+    constexpr int ne = (KIND == 0 || RECON == 18) ? 9 : 6;  // stored elements per matrix
+    float4 q[nq];
+#pragma unroll
+    for (int k = 0; k < nq; ++k) q[k] = ld_stream_f4(base + ((size_t)k * S + i) * 16, pol);
+    float f[4 * nq];
+#pragma unroll
+    for (int k = 0; k < nq; ++k) {
+      f[4 * k] = q[k].x; f[4 * k + 1] = q[k].y; f[4 * k + 2] = q[k].z; f[4 * k + 3] = q[k].w;
+    }
+#pragma unroll
+    for (int e = 0; e < ne; ++e) {
+      m[0].e[e] = make_float2(f[2 * e], f[2 * e + 1]);
+      m[1].e[e] = make_float2(f[2 * ne + 2 * e], f[2 * ne + 2 * e + 1]);
+    }
+    if constexpr (ne == 6) {
+      reconstruct_row2(m[0], ls.recon_f);
+      reconstruct_row2(m[1], ls.recon_f);
+    }
+  }
   static __device__ __forceinline__ void load(const char *links, int S, int i, int mu,
                                               const LinkScales &ls, Mat3<float> m[4]) {
     const char *fat = links + (size_t)mu * LL::mu_bytes * S;
     const char *lng = fat + (size_t)LL::fat_bytes * S;
+    const uint64_t pol = l2_evict_first_policy();
     float4 q[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) q[k] = ld_stream_f4(fat + ((size_t)k * S + i) * 16);
+    for (int k = 0; k < 9; ++k) q[k] = ld_stream_f4(fat + ((size_t)k * S + i) * 16, pol);
     // floats 0..17 -> F_mu(x), 18..35 -> F_mu(x-mu)^dag
     float f[36];
 #pragma unroll
@@ -362,7 +401,7 @@ template <int RECON> struct LinkIO<PREC_F32, RECON> {
     }
     if (RECON == 18) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) q[k] = ld_stream_f4(lng + ((size_t)k * S + i) * 16);
+      for (int k = 0; k < 9; ++k) q[k] = ld_stream_f4(lng + ((size_t)k * S + i) * 16, pol);
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         f[4 * k] = q[k].x; f[4 * k + 1] = q[k].y; f[4 * k + 2] = q[k].z; f[4 * k + 3] = q[k].w;
@@ -374,7 +413,7 @@ template <int RECON> struct LinkIO<PREC_F32, RECON> {
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) q[k] = ld_stream_f4(lng + ((size_t)k * S + i) * 16);
+      for (int k = 0; k < 6; ++k) q[k] = ld_stream_f4(lng + ((size_t)k * S + i) * 16, pol);
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
         f[4 * k] = q[k].x; f[4 * k + 1] = q[k].y; f[4 * k + 2] = q[k].z; f[4 * k + 3] = q[k].w;
@@ -398,14 +437,15 @@ template <int RECON> struct LinkIO<PREC_I16, RECON> {
                                               const LinkScales &ls, Mat3<float> m[4]) {
     const char *fat = links + (size_t)mu * LL::mu_bytes * S;
     const char *lng = fat + (size_t)LL::fat_bytes * S;
+    const uint64_t pol = l2_evict_first_policy();
     uint32_t w[18];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      uint4 q = ld_stream_u4(fat + ((size_t)k * S + i) * 16);
+      uint4 q = ld_stream_u4(fat + ((size_t)k * S + i) * 16, pol);
       w[4 * k] = q.x; w[4 * k + 1] = q.y; w[4 * k + 2] = q.z; w[4 * k + 3] = q.w;
     }
     {
-      uint2 q = ld_stream_u2(fat + (size_t)64 * S + (size_t)i * 8);
+      uint2 q = ld_stream_u2(fat + (size_t)64 * S + (size_t)i * 8, pol);
       w[16] = q.x; w[17] = q.y;
     }
 #pragma unroll
@@ -416,10 +456,10 @@ template <int RECON> struct LinkIO<PREC_I16, RECON> {
     if (RECON == 18) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        uint4 q = ld_stream_u4(lng + ((size_t)k * S + i) * 16);
+        uint4 q = ld_stream_u4(lng + ((size_t)k * S + i) * 16, pol);
         w[4 * k] = q.x; w[4 * k + 1] = q.y; w[4 * k + 2] = q.z; w[4 * k + 3] = q.w;
       }
-      uint2 q = ld_stream_u2(lng + (size_t)64 * S + (size_t)i * 8);
+      uint2 q = ld_stream_u2(lng + (size_t)64 * S + (size_t)i * 8, pol);
       w[16] = q.x; w[17] = q.y;
 #pragma unroll
       for (int e = 0; e < 9; ++e) {
@@ -429,7 +469,7 @@ template <int RECON> struct LinkIO<PREC_I16, RECON> {
     } else {
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        uint4 q = ld_stream_u4(lng + ((size_t)k * S + i) * 16);
+        uint4 q = ld_stream_u4(lng + ((size_t)k * S + i) * 16, pol);
         w[4 * k] = q.x; w[4 * k + 1] = q.y; w[4 * k + 2] = q.z; w[4 * k + 3] = q.w;
       }
 #pragma unroll

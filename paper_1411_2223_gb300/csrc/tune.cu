@@ -27,7 +27,7 @@ struct Tuner {
 
 static std::string tune_key(const Geom &g, int prec, int recon, int nrhs, int mode) {
   std::ostringstream s;
-  s << "dslash_v2:" << g.L[0] << "x" << g.L[1] << "x" << g.L[2] << "x" << g.L[3] << ":p" << prec
+  s << "dslash_v3:" << g.L[0] << "x" << g.L[1] << "x" << g.L[2] << "x" << g.L[3] << ":p" << prec
     << ":r" << recon << ":n" << nrhs << ":m" << mode;
   return s.str();
 }
@@ -122,9 +122,11 @@ DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon
     a.counter = counter;
     a.gate = GATE_RUNNING;
   }
+  // RHS tiles; the many-RHS tiles (8, 12) exist for the FP32 kernels only
+  // (launch_dslash refuses the others and the candidate is skipped)
   std::vector<int> nrs = {1};
-  if (nrhs >= 2) nrs.push_back(2);
-  if (nrhs >= 4) nrs.push_back(4);
+  for (int nr : {2, 4, 8, 12})
+    if (nrhs >= nr) nrs.push_back(nr);
   float best = 1e30f;
   DslashConfig best_c = def;
   const int reps = 5;

@@ -82,6 +82,8 @@ SIGNATURES = {
     'sq_kernel_launches': (_U64, [_P]),
     'gauge_load': (_I, [_P, _P, _P, _P, _U, ctypes.POINTER(_I)]),
     'gauge_free': (_I, [_P, _I]),
+    'gauge_fatten': (_I, [_P, _P, _P, _D, _D, _D, _P, _P, _P]),
+    'gauge_load_thin': (_I, [_P, _P, _P, _D, _D, _D, _U, ctypes.POINTER(_I)]),
     'sq_spinor_bytes': (_I, [_P, _I, _I, ctypes.POINTER(_SZ), ctypes.POINTER(_I)]),
     'sq_pack_spinor': (_I, [_P, _I, _I, _P, _P, _P]),
     'sq_unpack_spinor': (_I, [_P, _I, _I, _P, _P, _P]),
@@ -203,6 +205,32 @@ class Context:
         _check(self._lib.gauge_load(self.handle, dims_a, _ptr(fat), _ptr(lng), flags,
                                     ctypes.byref(gid)), 'gauge_load')
         self._dims[gid.value] = tuple(int(d) for d in dims)
+        return gid.value
+
+    def gauge_fatten(self, dims, thin_dev, fat_dev, lng_dev, c1=9.0 / 8.0, c3=-1.0 / 24.0,
+                     staple_weight=0.1, stream=None):
+        """Fat and long links from thin links on the device (torch CUDA tensors
+        of shape (V, 4, 3, 3) complex128)."""
+        d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+        _check(self._lib.gauge_fatten(self.handle, d, _ptr(thin_dev), float(c1), float(c3),
+                                      float(staple_weight), _ptr(fat_dev), _ptr(lng_dev),
+                                      _stream(stream)), 'gauge_fatten')
+
+    def gauge_load_thin(self, dims, thin, c1=9.0 / 8.0, c3=-1.0 / 24.0, staple_weight=0.1,
+                        antiperiodic_t=False, flags=0):
+        """Fatten thin links on the GPU and load the result; returns a gauge id."""
+        d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+        if _is_device(thin):
+            flags |= GAUGE_DEVICE_PTRS
+            t = thin.contiguous()
+        else:
+            t = np.ascontiguousarray(thin, dtype=np.complex128)
+        if antiperiodic_t:
+            flags |= GAUGE_ANTIPERIODIC_T
+        gid = ctypes.c_int(0)
+        _check(self._lib.gauge_load_thin(self.handle, d, _ptr(t), float(c1), float(c3),
+                                         float(staple_weight), flags, ctypes.byref(gid)),
+               'gauge_load_thin')
         return gid.value
 
     def gauge_free(self, gauge_id):
@@ -407,7 +435,7 @@ def _forward(name):
     return f
 
 
-for _n in ('gauge_load', 'gauge_free', 'dslash_apply', 'mdagm_apply', 'cg_solve',
+for _n in ('gauge_load', 'gauge_free', 'gauge_fatten', 'gauge_load_thin', 'dslash_apply', 'mdagm_apply', 'cg_solve',
            'cg_solve_multi', 'cg_solve_multishift', 'cg_solve_full', 'dirac_apply',
            'serve_submit', 'serve_poll',
            'serve_cancel', 'serve_stats', 'serve_configure'):

@@ -141,3 +141,41 @@ def test_batched_full_size_24x64(sq):
             assert oracle.true_residual(dims, fat, lng, m, srcs[0], xm[i]) <= tol
     finally:
         sq.gauge_free(gid)
+
+
+@pytest.mark.parametrize('nr', [8, 12])
+@pytest.mark.parametrize('recon', [18, 12])
+def test_many_rhs_tiles_match_oracle(tmp_path, monkeypatch, nr, recon):
+    """The FP32 Dslash tiles that apply each link to 8 or 12 systems, forced
+    through a tuning cache file (SQ_TUNE_CACHE), solve every system of a
+    12-system batch to the oracle's acceptance, in the iteration counts of
+    the one-system tile (the two tiles add the 16 hop products in different
+    orders, so they agree to rounding, not bit for bit)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip('no CUDA device')
+    from paper_1411_2223_gb300 import sq as sqm
+    dims = (4, 6, 8, 10)
+    fat, lng = gauge(dims, 0.25, 0)
+    vh = oracle.volume(dims) // 2
+    nrhs = 12
+    srcs = synth.gaussian_sources(vh, range(20, 20 + nrhs))
+    masses = np.linspace(0.02, 0.2, nrhs)
+    tol = 1e-8
+    lat = 'x'.join(map(str, dims))
+    results = {}
+    for tile in (1, nr):
+        cache = tmp_path / ('tune_%d.txt' % tile)
+        cache.write_text(''.join('dslash_v3:%s:p1:r%d:n%d:m%d 128 %d\n' % (lat, recon, nrhs, m, tile)
+                                 for m in (0, 1)))
+        monkeypatch.setenv('SQ_TUNE_CACHE', str(cache))
+        with sqm.Context(0) as ctx:
+            gid = ctx.gauge_load(dims, fat, lng)
+            xs, stats, status = ctx.cg_solve_multi(gid, srcs, masses, tol, long_recon=recon)
+            assert status == 0
+        results[tile] = (xs, [s['iterations'] for s in stats])
+    xs, its = results[nr]
+    assert max(abs(a - b) for a, b in zip(its, results[1][1])) <= 4
+    for j in range(nrhs):
+        x_ref, _, _ = oracle.cg(dims, fat, lng, masses[j], srcs[j], 1e-12)
+        o9_check(dims, fat, lng, masses[j], srcs[j], xs[j], x_ref, tol)
