@@ -208,6 +208,8 @@ extern "C" int gauge_load(sq_ctx *ctx, const int dims[4], const double *fat, con
   g.vh = (int)(vol / 2);
   g.stride = (g.vh + 63) / 64 * 64;
   g.nchunks = (g.vh + CHUNK - 1) / CHUNK;
+  g.nwchunks = (g.vh + 31) / 32;
+  g.ngroups = (g.nwchunks + 31) / 32;
   g.t_antiperiodic = (flags & SQ_GAUGE_ANTIPERIODIC_T) ? 1 : 0;
   geom_set_divisor(g, 0, (uint32_t)g.lxh);
   geom_set_divisor(g, 1, (uint32_t)dims[1]);

@@ -12,29 +12,24 @@ namespace {
 
 __device__ __forceinline__ bool running(const SlotState *s) { return s->status == SLOT_RUNNING; }
 
-__device__ __forceinline__ bool any_running(const SlotState *s, int n) {
-  bool any = false;
-  for (int r = 0; r < n; ++r) any |= running(s + r);
-  return any;
-}
-
-// xs += alpha p ; r -= alpha Ap ; partial |r|^2 ; last block: finish_update
+// xs += alpha p ; r -= alpha Ap ; |r|^2 over the row's sites ; the warp that
+// completes the sum runs finish_update for this row's system.
 template <int S>
-__global__ void __launch_bounds__(256) cg_update_kernel(VecArgs a) {
+__global__ void __launch_bounds__(256, 8) cg_update_kernel(VecArgs a) {
   using R = typename SpinorIO<S>::R;
   constexpr int XP = (S == PREC_F64) ? PREC_F64 : PREC_F32;
-  if (!any_running(a.slots, a.nrhs)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
-  const int St = a.g.stride;
   SlotState *s = a.slots + r;
+  if (!running(s)) return;  // the same for every block of the row
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int St = a.g.stride;
   double val[1] = {0.0};
-  if (i < a.g.vh && running(s)) {
+  if (i < a.g.vh) {
     const R al = (R)s->alpha;
     Vec3<R> p = SpinorIO<S>::load(a.p + r * a.fb, St, i);
     Vec3<R> ap = SpinorIO<S>::load(a.ap + r * a.fb, St, i);
     Vec3<R> rv = SpinorIO<S>::load(a.r + r * a.fb, St, i);
-    Vec3<R> x = SpinorIO<XP>::load(a.xs + r * a.xs_fb, St, i);
+    Vec3<typename SpinorIO<XP>::R> x = SpinorIO<XP>::load(a.xs + r * a.xs_fb, St, i);
     R n2 = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -48,22 +43,16 @@ __global__ void __launch_bounds__(256) cg_update_kernel(VecArgs a) {
     SpinorIO<S>::store(a.r + r * a.fb, St, i, rv);
     val[0] = (double)n2;
   }
-  __shared__ double smem[8];
-  chunk_reduce<1>(val, smem, a.partial + (size_t)r * a.g.nchunks, a.g.nchunks);
-  if (last_block_arrived(a.counter, gridDim.x * gridDim.y)) {
-    __shared__ double red[32];
-    for (int k = 0; k < a.nrhs; ++k) {
-      if (!running(a.slots + k)) continue;
-      double rr = block_sum_fixed(a.partial + (size_t)k * a.g.nchunks, a.g.nchunks, red);
-      if (threadIdx.x == 0) finish_update(a.slots + k, rr, a.checkpoint);
-    }
-    if (threadIdx.x == 0) *a.counter = 0;
-  }
+  double *const inst[1] = {a.partial + (size_t)r * red_stride(a.g)};
+  double rr[1];
+  if (warp_tree_reduce<1>(val, 1, inst, a.g, a.counter + (size_t)r * ticket_stride(a.g), rr) &&
+      (threadIdx.x & 31) == 0)
+    finish_update(s, rr[0], a.checkpoint);
 }
 
 // p = a r + beta p (a complex, 1 except right after a reliable update)
 template <int S>
-__global__ void __launch_bounds__(256) cg_xpay_kernel(VecArgs a) {
+__global__ void __launch_bounds__(256, 8) cg_xpay_kernel(VecArgs a) {
   using R = typename SpinorIO<S>::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
@@ -88,15 +77,15 @@ __global__ void __launch_bounds__(256) cg_xpay_kernel(VecArgs a) {
 // block: finish_init.  Slots already iterating are left alone, so systems
 // can join a running batch.
 template <int S>
-__global__ void __launch_bounds__(256) cg_init_kernel(VecArgs a, int guess) {
+__global__ void __launch_bounds__(256, 8) cg_init_kernel(VecArgs a, int guess) {
   using R = typename SpinorIO<S>::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   const int St = a.g.stride;
   SlotState *s = a.slots + r;
-  const bool act = s->status == SLOT_INIT;
+  if (s->status != SLOT_INIT) return;  // the same for every block of the row
   double val[1] = {0.0};
-  if (i < a.g.vh && act) {
+  if (i < a.g.vh) {
     Vec3<double> b = SpinorIO<PREC_F64>::load(a.b64 + r * a.f64_fb, St, i);
     double n2 = 0;
 #pragma unroll
@@ -121,22 +110,15 @@ __global__ void __launch_bounds__(256) cg_init_kernel(VecArgs a, int guess) {
       SpinorIO<PREC_F64>::store(a.x64 + r * a.f64_fb, St, i, z);
     }
   }
-  __shared__ double smem[8];
-  chunk_reduce<1>(val, smem, a.partial + (size_t)r * a.g.nchunks, a.g.nchunks);
-  if (last_block_arrived(a.counter, gridDim.x * gridDim.y)) {
-    __shared__ double red[32];
-    for (int k = 0; k < a.nrhs; ++k) {
-      if (a.slots[k].status != SLOT_INIT) continue;
-      double b2 = block_sum_fixed(a.partial + (size_t)k * a.g.nchunks, a.g.nchunks, red);
-      if (threadIdx.x == 0) {
-        finish_init(a.slots + k, b2);
-        if (guess && a.slots[k].status == SLOT_RUNNING) {
-          a.slots[k].ru_pending = 1;
-          a.slots[k].status = SLOT_WAIT;
-        }
-      }
+  double *const inst[1] = {a.partial + (size_t)r * red_stride(a.g)};
+  double b2[1];
+  if (warp_tree_reduce<1>(val, 1, inst, a.g, a.counter + (size_t)r * ticket_stride(a.g), b2) &&
+      (threadIdx.x & 31) == 0) {
+    finish_init(s, b2[0]);
+    if (guess && s->status == SLOT_RUNNING) {
+      s->ru_pending = 1;
+      s->status = SLOT_WAIT;
     }
-    if (threadIdx.x == 0) *a.counter = 0;
   }
 }
 

@@ -313,19 +313,18 @@ dslash_kernel(const DslashArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r0 = blockIdx.y * NR;
 
-  // Gate: the decision is the same in every block (slot state only changes in
-  // the last block of a reduction kernel, after all blocks have read it).
+  // Gate: the decision is the same in every block of a tile row (a system's
+  // state only changes in the warp that completes a reduction over its row,
+  // after every block of the row has read it).  Rows are independent.
   bool active[NR];
   bool any_here = false;
   if (a.slots != nullptr && a.gate != GATE_NONE) {
-    bool any = false;
-    for (int r = 0; r < a.nrhs; ++r) any |= slot_active(a.slots + r, a.gate);
-    if (!any) return;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       active[r] = (r0 + r < a.nrhs) && slot_active(a.slots + r0 + r, a.gate);
       any_here |= active[r];
     }
+    if (!any_here) return;
   } else {
 #pragma unroll
     for (int r = 0; r < NR; ++r) active[r] = (r0 + r < a.nrhs);
@@ -430,21 +429,23 @@ dslash_kernel(const DslashArgs a) {
         dot[r] = (double)d;
       }
     }
-    if (a.slots != nullptr && a.partial != nullptr) {
-      __shared__ double smem[NR * 16];
-      chunk_reduce<NR>(dot, smem, a.partial + (size_t)r0 * g.nchunks, g.nchunks,
-                       min(NR, a.nrhs - r0));
-      if (last_block_arrived(a.counter, gridDim.x * gridDim.y)) {
-        __shared__ double red[32];
-        for (int r = 0; r < a.nrhs; ++r) {
-          if (!slot_active(a.slots + r, a.gate)) continue;
-          double pap = block_sum_fixed(a.partial + (size_t)r * g.nchunks, g.nchunks, red);
-          if (threadIdx.x == 0) {
-            finish_alpha(a.slots + r, pap);
-            if (a.shifts) finish_shift_alpha(a.slots + r, a.shifts, a.nshift);
-          }
+    if (a.slots != nullptr && a.partial != nullptr && any_here) {
+      // <p, Ap> of every system of this tile; the warp completing the sums
+      // sets alpha for the tile's running systems
+      double *inst[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        inst[r] = a.partial + (size_t)min(r0 + r, a.nrhs - 1) * red_stride(g);
+      double pap[NR];
+      if (warp_tree_reduce<NR>(dot, min(NR, a.nrhs - r0), inst, g,
+                               a.counter + (size_t)blockIdx.y * ticket_stride(g), pap) &&
+          (threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (!active[r]) continue;
+          finish_alpha(a.slots + r0 + r, pap[r]);
+          if (a.shifts) finish_shift_alpha(a.slots + r0 + r, a.shifts, a.nshift);
         }
-        if (threadIdx.x == 0) *a.counter = 0;
       }
     }
   } else {  // MODE_RESID (PREC == F64)
@@ -493,21 +494,28 @@ dslash_kernel(const DslashArgs a) {
         val[0][r] = n2; val[1][r] = pre; val[2][r] = pim;
       }
     }
-    __shared__ double smem[NR * 16];
+    if (any_here) {
+      // |r|^2, <r, p> of every system of this tile (value k*3 + v); the warp
+      // completing the sums finishes the tile's reliable updates
+      double vals[3 * NR];
+      double *inst[3 * NR];
 #pragma unroll
-    for (int v = 0; v < 3; ++v)
-      chunk_reduce<NR>(val[v], smem, a.partial + ((size_t)v * a.nrhs + r0) * g.nchunks, g.nchunks,
-                       min(NR, a.nrhs - r0));
-    if (last_block_arrived(a.counter, gridDim.x * gridDim.y)) {
-      __shared__ double red[32];
-      for (int r = 0; r < a.nrhs; ++r) {
-        if (!slot_active(a.slots + r, GATE_RU)) continue;
-        double s0 = block_sum_fixed(a.partial + ((size_t)0 * a.nrhs + r) * g.nchunks, g.nchunks, red);
-        double s1 = block_sum_fixed(a.partial + ((size_t)1 * a.nrhs + r) * g.nchunks, g.nchunks, red);
-        double s2 = block_sum_fixed(a.partial + ((size_t)2 * a.nrhs + r) * g.nchunks, g.nchunks, red);
-        if (threadIdx.x == 0) finish_reliable_update(a.slots + r, s0, s1, s2);
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          vals[3 * r + v] = val[v][r];
+          inst[3 * r + v] =
+              a.partial + ((size_t)v * a.nrhs + min(r0 + r, a.nrhs - 1)) * red_stride(g);
+        }
+      double out[3 * NR];
+      if (warp_tree_reduce<3 * NR>(vals, 3 * min(NR, a.nrhs - r0), inst, g,
+                                   a.counter + (size_t)blockIdx.y * ticket_stride(g), out) &&
+          (threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          if (active[r])
+            finish_reliable_update(a.slots + r0 + r, out[3 * r], out[3 * r + 1], out[3 * r + 2]);
       }
-      if (threadIdx.x == 0) *a.counter = 0;
     }
   }
 }

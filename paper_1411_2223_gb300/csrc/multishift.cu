@@ -62,12 +62,11 @@ __global__ void __launch_bounds__(256) ms_init_kernel(MsArgs a) {
       SpinorIO<XP>::store(a.x + k * a.xfb, St, i, z);
     }
   }
-  __shared__ double smem[8];
-  chunk_reduce<1>(val, smem, a.partial, a.g.nchunks);
-  if (last_block_arrived(a.counter, gridDim.x)) {
-    __shared__ double red[32];
-    double b2 = block_sum_fixed(a.partial, a.g.nchunks, red);
-    if (threadIdx.x == 0) {
+  double *const inst[1] = {a.partial};
+  double sum[1];
+  if (warp_tree_reduce<1>(val, 1, inst, a.g, a.counter, sum)) {
+    if ((threadIdx.x & 31) == 0) {
+      const double b2 = sum[0];
       finish_init(a.bs, b2);
       a.bs->alpha_prev = 1.0;
       a.bs->beta_prev = 0.0;
@@ -79,7 +78,6 @@ __global__ void __launch_bounds__(256) ms_init_kernel(MsArgs a) {
         s.active = s.cont = (a.bs->status == SLOT_RUNNING);
         s.iter = 0;
       }
-      *a.counter = 0;
     }
   }
 }
@@ -106,16 +104,10 @@ __global__ void __launch_bounds__(256) ms_update_kernel(MsArgs a) {
     SpinorIO<S>::store(a.r, St, i, rv);
     val[0] = (double)n2;
   }
-  __shared__ double smem[8];
-  chunk_reduce<1>(val, smem, a.partial, a.g.nchunks);
-  if (last_block_arrived(a.counter, gridDim.x)) {
-    __shared__ double red[32];
-    double rr = block_sum_fixed(a.partial, a.g.nchunks, red);
-    if (threadIdx.x == 0) {
-      finish_shift_update(a.bs, a.sh, a.nshift, rr);
-      *a.counter = 0;
-    }
-  }
+  double *const inst[1] = {a.partial};
+  double rr[1];
+  if (warp_tree_reduce<1>(val, 1, inst, a.g, a.counter, rr) && (threadIdx.x & 31) == 0)
+    finish_shift_update(a.bs, a.sh, a.nshift, rr[0]);
 }
 
 // x_i += alpha_i p_i ; p_i = zeta_i r + beta_i p_i ; the last block closes
@@ -156,11 +148,12 @@ __global__ void __launch_bounds__(256) ms_xpay_kernel(MsArgs a) {
       }
     }
   }
-  if (last_block_arrived(a.counter + 1, gridDim.x)) {
+  unsigned *close = a.counter + ticket_stride(a.g);
+  if (last_block_arrived(close, gridDim.x)) {
     if (threadIdx.x == 0) {
       for (int k = 0; k < a.nshift; ++k) a.sh[k].active = a.sh[k].cont;
       if (a.bs->status == SLOT_WAIT) a.bs->status = a.bs->final_status;
-      a.counter[1] = 0;
+      *close = 0;
     }
   }
 }
@@ -241,7 +234,7 @@ int ms_work_get(sq_ctx *ctx, GaugeField *gf, int gid, int prec, int recon, int n
   const size_t canon_b = (size_t)3 * g.vh * 16;
   size_t sizes[] = {w->f64_fb, w->fb, w->fb, w->fb, w->fb * nshift, w->xfb * nshift,
                     2 * canon_b * nshift, sizeof(SlotState), sizeof(ShiftState) * nshift,
-                    sizeof(double) * g.nchunks, sizeof(unsigned) * 4};
+                    sizeof(double) * red_stride(g), sizeof(unsigned) * (2 * ticket_stride(g) + 4)};
   char **ptrs[] = {&w->b64, &w->r, &w->ap, &w->t, &w->p, &w->x};
   size_t total = 0;
   for (size_t s : sizes) total += s;
@@ -311,7 +304,7 @@ int ms_enqueue_iteration(MsWork *w, cudaStream_t st) {
   b.out = w->ap;
   b.p = pb;
   b.partial = w->partial;
-  b.counter = w->counters + 2;
+  b.counter = w->counters + ticket_stride(g) + 1;
   b.shifts = w->sh_d;
   b.nshift = w->nshift;
   if (launch_dslash(w->prec, w->recon, 1, MODE_MDAGM, w->prec, b, w->cfg_mdagm.block, st))

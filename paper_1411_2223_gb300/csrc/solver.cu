@@ -49,11 +49,12 @@ int cg_work_create(sq_ctx *ctx, GaugeField *gf, int prec, int recon, int nrhs, C
   w->f64_fb = spinor_bytes(PREC_F64, g.stride);
   w->fb = spinor_bytes(prec, g.stride);
   w->xs_fb = spinor_bytes(xs_prec(prec), g.stride);
-  w->partial_stride = (size_t)3 * nrhs * g.nchunks;
+  w->partial_stride = (size_t)3 * nrhs * red_stride(g);
+  w->counter_stride = (size_t)nrhs * ticket_stride(g);
   size_t sizes[] = {w->f64_fb * nrhs, w->f64_fb * nrhs, w->f64_fb * nrhs, w->fb * nrhs,
                     w->fb * nrhs,     w->fb * nrhs,     w->fb * nrhs,     w->xs_fb * nrhs,
                     sizeof(SlotState) * nrhs, sizeof(double) * 4 * w->partial_stride,
-                    sizeof(unsigned) * 8};
+                    sizeof(unsigned) * 4 * w->counter_stride};
   char **ptrs[] = {&w->x64, &w->b64, &w->t64, &w->r, &w->p, &w->ap, &w->t, &w->xs};
   size_t total = 0;
   for (size_t s : sizes) total += s;
@@ -119,7 +120,7 @@ static VecArgs vec_args(CGWork *w, int region) {
   a.xs_fb = w->xs_fb;
   a.slots = w->slots_d;
   a.partial = w->partial + region * w->partial_stride;
-  a.counter = w->counters + region;
+  a.counter = w->counters + region * w->counter_stride;
   a.checkpoint = 0;
   return a;
 }
@@ -187,7 +188,7 @@ int cg_enqueue_ru(CGWork *w, cudaStream_t st) {
   b.ps = w->p;
   b.ps_fb = w->fb;
   b.partial = w->partial + 2 * w->partial_stride;
-  b.counter = w->counters + 2;
+  b.counter = w->counters + 2 * w->counter_stride;
   b.gate = GATE_RU;
   return check_launch(w->ctx, launch_dslash(PREC_F64, 18, w->cfg_ru_resid.nr, MODE_RESID,
                                             w->prec, b, w->cfg_ru_resid.block, st));
@@ -216,7 +217,7 @@ int cg_enqueue_iteration(CGWork *w, cudaStream_t st, int checkpoint) {
   b.p = w->p;
   b.p_fb = w->fb;
   b.partial = w->partial;
-  b.counter = w->counters + 0;
+  b.counter = w->counters;
   b.gate = GATE_RUNNING;
   rc = check_launch(w->ctx, launch_dslash(w->prec, w->recon, w->cfg_mdagm.nr, MODE_MDAGM,
                                           w->prec, b, w->cfg_mdagm.block, st));

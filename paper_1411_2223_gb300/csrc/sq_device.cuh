@@ -548,6 +548,73 @@ __device__ __forceinline__ bool last_block_arrived(unsigned *counter, unsigned t
   return is_last;
 }
 
+// Barrier-free reduction over the sites of a grid row, in a fixed order.
+// Every warp covers 32 consecutive sites (blockDim a multiple of 32) and
+// writes the shuffle-tree sum of its NV values as one partial per value.
+// Warps are grouped 32 at a time by site index: the warp that arrives last in
+// its group (one acquire-release ticket per group) adds the group's partials
+// with a shuffle tree; the group that finishes last (a second ticket) adds
+// the group sums, each lane over groups lane, lane + 32, ... in order, then a
+// shuffle tree.  The order depends on site indices only, so every launch
+// shape gives the same bits, and no block ever waits at a barrier.
+//   inst[v]  base of value v's instance: nwchunks warp partials, then
+//            ngroups group sums (red_stride doubles)
+//   tickets  ngroups + 1 counters of this row (zero on entry; left zero)
+// Returns true in every lane of the single warp that completed the sums;
+// out[v] then holds sum v (all lanes).  All 32 lanes of each warp must call
+// it together.
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+               : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+template <int NV>
+__device__ __forceinline__ bool warp_tree_reduce(const double (&val)[NV], int nvalid,
+                                                 double *const (&inst)[NV], const Geom &g,
+                                                 unsigned *tickets, double (&out)[NV]) {
+  const int lane = threadIdx.x & 31;
+  const int wc = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (wc >= g.nwchunks) return false;  // a warp wholly past the last site
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double sv = warp_sum(val[v]);
+    if (lane == 0 && v < nvalid) inst[v][wc] = sv;
+  }
+  const int grp = wc >> 5;
+  const int in_grp = min(32, g.nwchunks - grp * 32);
+  unsigned t = 0;
+  if (lane == 0) t = atom_add_acq_rel(tickets + grp, 1u);
+  t = __shfl_sync(0xffffffffu, t, 0);
+  if (t != (unsigned)(in_grp - 1)) return false;
+  __syncwarp();
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if (v >= nvalid) break;
+    const double x = (lane < in_grp) ? __ldcg(inst[v] + grp * 32 + lane) : 0.0;
+    const double gs = warp_sum(x);
+    if (lane == 0) inst[v][g.nwchunks + grp] = gs;
+  }
+  if (lane == 0) {
+    tickets[grp] = 0;
+    t = atom_add_acq_rel(tickets + g.ngroups, 1u);
+  }
+  t = __shfl_sync(0xffffffffu, t, 0);
+  if (t != (unsigned)(g.ngroups - 1)) return false;
+  __syncwarp();
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    out[v] = 0.0;
+    if (v >= nvalid) continue;
+    double acc = 0.0;
+    for (int k = lane; k < g.ngroups; k += 32) acc += __ldcg(inst[v] + g.nwchunks + k);
+    out[v] = warp_sum(acc);
+  }
+  if (lane == 0) tickets[g.ngroups] = 0;
+  return true;
+}
+
 // Fixed-order sum of n partials: 128 virtual lanes (the block's first 128
 // threads) accumulate strided elements in order k, k + 128, k + 256, ...,
 // then a fixed shuffle tree and the four warp sums in order.  Independent of

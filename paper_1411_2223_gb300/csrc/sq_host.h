@@ -100,6 +100,7 @@ struct CGWork {
   unsigned *counters = nullptr;
   size_t bytes = 0;
   size_t partial_stride = 0;  // doubles per reduction region
+  size_t counter_stride = 0;  // ticket counters per reduction region
   cudaGraphExec_t exec = nullptr;
   int exec_iters = 0;
   int exec_kernels = 0;       // kernels per replay

@@ -4,6 +4,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#ifdef __CUDACC__
+#define SQ_HD __host__ __device__
+#else
+#define SQ_HD
+#endif
+
 namespace sq {
 
 enum Prec { PREC_F64 = 0, PREC_F32 = 1, PREC_I16 = 2 };
@@ -16,6 +22,8 @@ struct Geom {
   int vh;              // sites per parity
   int stride;          // plane stride in sites (vh rounded up to 64)
   int nchunks;         // ceil(vh / CHUNK)
+  int nwchunks;        // ceil(vh / 32): one partial per warp of 32 sites
+  int ngroups;         // ceil(nwchunks / 32): groups of 32 warp partials
   int t_antiperiodic;  // 1: hops wrapping around t pick up -1
   // exact division by Lx/2, Ly, Lz with a multiply-high (Granlund-Montgomery)
   uint32_t div_m[3];
@@ -32,6 +40,11 @@ inline void geom_set_divisor(Geom &g, int k, uint32_t d) {
   g.div_s1[k] = l > 0 ? 1 : 0;
   g.div_s2[k] = l > 0 ? l - 1 : 0;
 }
+
+// Doubles of one reduction instance (warp partials, then group sums) and
+// unsigned counters of one ticket set (per group, then the final one).
+SQ_HD inline size_t red_stride(const Geom &g) { return (size_t)g.nwchunks + g.ngroups; }
+SQ_HD inline size_t ticket_stride(const Geom &g) { return (size_t)g.ngroups + 1; }
 
 // Bytes of one packed parity-half colour vector.
 inline size_t spinor_bytes(int prec, int stride) {

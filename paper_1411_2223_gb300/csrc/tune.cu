@@ -75,7 +75,8 @@ DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon
   size_t fb = spinor_bytes(prec, g.stride);
   void *in = nullptr, *out = nullptr, *aux = nullptr;
   // aux: p field, slot states, partial sums and the ticket counter (MDAGM)
-  size_t aux_b = fb * nrhs + sizeof(SlotState) * nrhs + sizeof(double) * nrhs * g.nchunks + 256;
+  size_t aux_b = fb * nrhs + sizeof(SlotState) * nrhs + sizeof(double) * nrhs * red_stride(g) +
+                 sizeof(unsigned) * nrhs * ticket_stride(g) + 256;
   if (cudaMalloc(&in, fb * nrhs) != cudaSuccess) return def;
   if (cudaMalloc(&out, fb * nrhs) != cudaSuccess || cudaMalloc(&aux, aux_b) != cudaSuccess) {
     cudaFree(in);
@@ -87,7 +88,7 @@ DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon
   char *auxc = static_cast<char *>(aux);
   SlotState *slots = reinterpret_cast<SlotState *>(auxc + fb * nrhs);
   double *partial = reinterpret_cast<double *>(slots + nrhs);
-  unsigned *counter = reinterpret_cast<unsigned *>(partial + (size_t)nrhs * g.nchunks);
+  unsigned *counter = reinterpret_cast<unsigned *>(partial + (size_t)nrhs * red_stride(g));
   if (mode == MODE_MDAGM) {
     std::vector<SlotState> hs(nrhs);
     for (auto &s : hs) {

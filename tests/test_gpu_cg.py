@@ -208,3 +208,30 @@ def test_config3_full_size_32x64_i16(sq):
         assert rel(got, want) <= TOL_DSLASH['i16']
     finally:
         sq.gauge_free(gid)
+
+
+def test_solution_bits_independent_of_block_size(tmp_path, monkeypatch):
+    """Every reduction sums in an order fixed by site indices, so the launch
+    shape the tuner picks cannot change a result: block sizes forced through
+    the tuning cache (SQ_TUNE_CACHE) give the same bits."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip('no CUDA device')
+    from paper_1411_2223_gb300 import sq as sqm
+    dims = (4, 6, 8, 10)
+    fat, lng = gauge(dims, 0.25, 0)
+    b = synth.gaussian_source(oracle.volume(dims) // 2, 7)
+    lat = 'x'.join(map(str, dims))
+    xs = []
+    for block in (128, 256, 512):
+        cache = tmp_path / ('tune_%d.txt' % block)
+        cache.write_text(''.join('dslash_v3:%s:p%d:r18:n1:m%d %d 1\n' % (lat, p, m, block)
+                                 for p in (0, 1) for m in (0, 1)))
+        monkeypatch.setenv('SQ_TUNE_CACHE', str(cache))
+        with sqm.Context(0) as ctx:
+            gid = ctx.gauge_load(dims, fat, lng)
+            x, st = ctx.cg_solve(gid, b, 0.05, 1e-9)
+            assert st['status'] == 0
+        xs.append(x)
+    assert np.array_equal(xs[0], xs[1]) and np.array_equal(xs[0], xs[2])
+    assert oracle.true_residual(dims, fat, lng, 0.05, b, xs[0]) <= 1e-9
