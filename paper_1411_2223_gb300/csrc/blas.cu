@@ -16,6 +16,8 @@ __device__ __forceinline__ bool running(const SlotState *s) { return s->status =
 // completes the sum runs finish_update for this row's system.
 template <int S>
 __global__ void __launch_bounds__(256, 8) cg_update_kernel(VecArgs a) {
+  griddep_launch_dependents();
+  griddep_wait();
   using R = typename SpinorIO<S>::R;
   constexpr int XP = (S == PREC_F64) ? PREC_F64 : PREC_F32;
   const int r = blockIdx.y;
@@ -45,14 +47,16 @@ __global__ void __launch_bounds__(256, 8) cg_update_kernel(VecArgs a) {
   }
   double *const inst[1] = {a.partial + (size_t)r * red_stride(a.g)};
   double rr[1];
-  if (warp_tree_reduce<1>(val, 1, inst, a.g, a.counter + (size_t)r * ticket_stride(a.g), rr) &&
-      (threadIdx.x & 31) == 0)
+  unsigned *tickets = a.counter + (size_t)r * ticket_stride(a.g);
+  if (warp_tree_reduce<1>(val, 1, inst, a.g, i, tickets, rr) && (threadIdx.x & 31) == 0)
     finish_update(s, rr[0], a.checkpoint);
 }
 
 // p = a r + beta p (a complex, 1 except right after a reliable update)
 template <int S>
 __global__ void __launch_bounds__(256, 8) cg_xpay_kernel(VecArgs a) {
+  griddep_launch_dependents();
+  griddep_wait();
   using R = typename SpinorIO<S>::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
@@ -78,6 +82,8 @@ __global__ void __launch_bounds__(256, 8) cg_xpay_kernel(VecArgs a) {
 // can join a running batch.
 template <int S>
 __global__ void __launch_bounds__(256, 8) cg_init_kernel(VecArgs a, int guess) {
+  griddep_launch_dependents();
+  griddep_wait();
   using R = typename SpinorIO<S>::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
@@ -112,8 +118,8 @@ __global__ void __launch_bounds__(256, 8) cg_init_kernel(VecArgs a, int guess) {
   }
   double *const inst[1] = {a.partial + (size_t)r * red_stride(a.g)};
   double b2[1];
-  if (warp_tree_reduce<1>(val, 1, inst, a.g, a.counter + (size_t)r * ticket_stride(a.g), b2) &&
-      (threadIdx.x & 31) == 0) {
+  unsigned *tickets = a.counter + (size_t)r * ticket_stride(a.g);
+  if (warp_tree_reduce<1>(val, 1, inst, a.g, i, tickets, b2) && (threadIdx.x & 31) == 0) {
     finish_init(s, b2[0]);
     if (guess && s->status == SLOT_RUNNING) {
       s->ru_pending = 1;
@@ -169,9 +175,9 @@ int launch_cg_update(int prec, const VecArgs &a, cudaStream_t st) {
   if (a.g.vh <= 0) return 0;
   dim3 grid = grid_for(a.g, 256, a.nrhs);
   switch (prec) {
-    case PREC_F64: cg_update_kernel<PREC_F64><<<grid, 256, 0, st>>>(a); break;
-    case PREC_F32: cg_update_kernel<PREC_F32><<<grid, 256, 0, st>>>(a); break;
-    case PREC_I16: cg_update_kernel<PREC_I16><<<grid, 256, 0, st>>>(a); break;
+    case PREC_F64: if (launch_pdl(cg_update_kernel<PREC_F64>, grid, dim3(256), 0, st, a)) return -1; break;
+    case PREC_F32: if (launch_pdl(cg_update_kernel<PREC_F32>, grid, dim3(256), 0, st, a)) return -1; break;
+    case PREC_I16: if (launch_pdl(cg_update_kernel<PREC_I16>, grid, dim3(256), 0, st, a)) return -1; break;
     default: return -1;
   }
   return 0;
@@ -181,9 +187,9 @@ int launch_cg_xpay(int prec, const VecArgs &a, cudaStream_t st) {
   if (a.g.vh <= 0) return 0;
   dim3 grid = grid_for(a.g, 256, a.nrhs);
   switch (prec) {
-    case PREC_F64: cg_xpay_kernel<PREC_F64><<<grid, 256, 0, st>>>(a); break;
-    case PREC_F32: cg_xpay_kernel<PREC_F32><<<grid, 256, 0, st>>>(a); break;
-    case PREC_I16: cg_xpay_kernel<PREC_I16><<<grid, 256, 0, st>>>(a); break;
+    case PREC_F64: if (launch_pdl(cg_xpay_kernel<PREC_F64>, grid, dim3(256), 0, st, a)) return -1; break;
+    case PREC_F32: if (launch_pdl(cg_xpay_kernel<PREC_F32>, grid, dim3(256), 0, st, a)) return -1; break;
+    case PREC_I16: if (launch_pdl(cg_xpay_kernel<PREC_I16>, grid, dim3(256), 0, st, a)) return -1; break;
     default: return -1;
   }
   return 0;
@@ -193,9 +199,9 @@ int launch_cg_init(int prec, const VecArgs &a, int guess, cudaStream_t st) {
   if (a.g.vh <= 0) return 0;
   dim3 grid = grid_for(a.g, 256, a.nrhs);
   switch (prec) {
-    case PREC_F64: cg_init_kernel<PREC_F64><<<grid, 256, 0, st>>>(a, guess); break;
-    case PREC_F32: cg_init_kernel<PREC_F32><<<grid, 256, 0, st>>>(a, guess); break;
-    case PREC_I16: cg_init_kernel<PREC_I16><<<grid, 256, 0, st>>>(a, guess); break;
+    case PREC_F64: if (launch_pdl(cg_init_kernel<PREC_F64>, grid, dim3(256), 0, st, a, guess)) return -1; break;
+    case PREC_F32: if (launch_pdl(cg_init_kernel<PREC_F32>, grid, dim3(256), 0, st, a, guess)) return -1; break;
+    case PREC_I16: if (launch_pdl(cg_init_kernel<PREC_I16>, grid, dim3(256), 0, st, a, guess)) return -1; break;
     default: return -1;
   }
   return 0;

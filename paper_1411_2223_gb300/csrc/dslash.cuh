@@ -310,8 +310,14 @@ dslash_kernel(const DslashArgs a) {
   using R = typename AccumType<PREC>::R;
   const Geom &g = a.g;
   const int S = g.stride;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r0 = blockIdx.y * NR;
+  griddep_launch_dependents();
+  griddep_wait();
+  // Blocks of the RHS tiles of one range of sites are adjacent in the launch
+  // order, so the tiles after the first find that range's links in L2.
+  const int ntiles = (a.nrhs + NR - 1) / NR;
+  const int tile = blockIdx.x % ntiles;
+  const int i = (blockIdx.x / ntiles) * blockDim.x + threadIdx.x;
+  const int r0 = tile * NR;
 
   // Gate: the decision is the same in every block of a tile row (a system's
   // state only changes in the warp that completes a reduction over its row,
@@ -437,8 +443,8 @@ dslash_kernel(const DslashArgs a) {
       for (int r = 0; r < NR; ++r)
         inst[r] = a.partial + (size_t)min(r0 + r, a.nrhs - 1) * red_stride(g);
       double pap[NR];
-      if (warp_tree_reduce<NR>(dot, min(NR, a.nrhs - r0), inst, g,
-                               a.counter + (size_t)blockIdx.y * ticket_stride(g), pap) &&
+      if (warp_tree_reduce<NR>(dot, min(NR, a.nrhs - r0), inst, g, i,
+                               a.counter + (size_t)tile * ticket_stride(g), pap) &&
           (threadIdx.x & 31) == 0) {
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
@@ -508,8 +514,8 @@ dslash_kernel(const DslashArgs a) {
               a.partial + ((size_t)v * a.nrhs + min(r0 + r, a.nrhs - 1)) * red_stride(g);
         }
       double out[3 * NR];
-      if (warp_tree_reduce<3 * NR>(vals, 3 * min(NR, a.nrhs - r0), inst, g,
-                                   a.counter + (size_t)blockIdx.y * ticket_stride(g), out) &&
+      if (warp_tree_reduce<3 * NR>(vals, 3 * min(NR, a.nrhs - r0), inst, g, i,
+                                   a.counter + (size_t)tile * ticket_stride(g), out) &&
           (threadIdx.x & 31) == 0) {
 #pragma unroll
         for (int r = 0; r < NR; ++r)

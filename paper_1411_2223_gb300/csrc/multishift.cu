@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) ms_init_kernel(MsArgs a) {
   }
   double *const inst[1] = {a.partial};
   double sum[1];
-  if (warp_tree_reduce<1>(val, 1, inst, a.g, a.counter, sum)) {
+  if (warp_tree_reduce<1>(val, 1, inst, a.g, i, a.counter, sum)) {
     if ((threadIdx.x & 31) == 0) {
       const double b2 = sum[0];
       finish_init(a.bs, b2);
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(256) ms_update_kernel(MsArgs a) {
   }
   double *const inst[1] = {a.partial};
   double rr[1];
-  if (warp_tree_reduce<1>(val, 1, inst, a.g, a.counter, rr) && (threadIdx.x & 31) == 0)
+  if (warp_tree_reduce<1>(val, 1, inst, a.g, i, a.counter, rr) && (threadIdx.x & 31) == 0)
     finish_shift_update(a.bs, a.sh, a.nshift, rr[0]);
 }
 

@@ -80,6 +80,21 @@ __device__ __forceinline__ float eta_sign(const SiteCoords &s, int mu) {
   return (sum & 1) ? -1.f : 1.f;
 }
 
+// ------------------------------------------------- dependent launches
+// The CG's kernels are launched with programmatic stream serialization: the
+// next kernel may be launched while the previous one drains, and waits in
+// griddep_wait() until that kernel has completed and its writes are visible.
+// Nothing written by the previous kernel may be touched before that call.
+// griddep_launch_dependents() allows the next kernel to launch once every
+// block of this one has passed it.  Without the launch attribute both are
+// no-ops.
+__device__ __forceinline__ void griddep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ----------------------------------------------------------- complex types
 
 template <typename R> struct C2;
@@ -549,7 +564,8 @@ __device__ __forceinline__ bool last_block_arrived(unsigned *counter, unsigned t
 }
 
 // Barrier-free reduction over the sites of a grid row, in a fixed order.
-// Every warp covers 32 consecutive sites (blockDim a multiple of 32) and
+// Every warp covers 32 consecutive sites (`site` is the calling thread's site
+// index, consecutive across the lanes of a warp; blockDim a multiple of 32) and
 // writes the shuffle-tree sum of its NV values as one partial per value.
 // Warps are grouped 32 at a time by site index: the warp that arrives last in
 // its group (one acquire-release ticket per group) adds the group's partials
@@ -573,9 +589,10 @@ __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
 template <int NV>
 __device__ __forceinline__ bool warp_tree_reduce(const double (&val)[NV], int nvalid,
                                                  double *const (&inst)[NV], const Geom &g,
-                                                 unsigned *tickets, double (&out)[NV]) {
+                                                 int site, unsigned *tickets,
+                                                 double (&out)[NV]) {
   const int lane = threadIdx.x & 31;
-  const int wc = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int wc = site >> 5;
   if (wc >= g.nwchunks) return false;  // a warp wholly past the last site
 #pragma unroll
   for (int v = 0; v < NV; ++v) {

@@ -24,6 +24,24 @@ struct VecArgs {
   int checkpoint;     // update kernel: a reliable update may follow this iteration
 };
 
+// Launch with programmatic stream serialization (the kernel must call
+// griddep_wait() before it reads anything the previous kernel wrote).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Precision of the solution increment for a sloppy precision.
 inline int xs_prec(int prec) { return prec == PREC_F64 ? PREC_F64 : PREC_F32; }
 
