@@ -15,23 +15,29 @@ __device__ __forceinline__ bool running(const SlotState *s) { return s->status =
 // xs += alpha p ; r -= alpha Ap ; |r|^2 over the row's sites ; the warp that
 // completes the sum runs finish_update for this row's system.
 template <int S>
-__global__ void __launch_bounds__(256, 8) cg_update_kernel(VecArgs a) {
-  griddep_launch_dependents();
-  griddep_wait();
+__global__ void __launch_bounds__(256, S == PREC_F64 ? 4 : 8) cg_update_kernel(VecArgs a) {
   using R = typename SpinorIO<S>::R;
   constexpr int XP = (S == PREC_F64) ? PREC_F64 : PREC_F32;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
+  const int St = a.g.stride;
+  // p, r and xs were last written at least two kernels back: load them
+  // before waiting for the predecessor (which writes Ap and alpha)
+  Vec3<R> p, rv;
+  Vec3<typename SpinorIO<XP>::R> x;
+  if (i < a.g.vh) {
+    p = SpinorIO<S>::load(a.p + r * a.fb, St, i);
+    rv = SpinorIO<S>::load(a.r + r * a.fb, St, i);
+    x = SpinorIO<XP>::load(a.xs + r * a.xs_fb, St, i);
+  }
+  griddep_wait();
+  griddep_launch_dependents();
   SlotState *s = a.slots + r;
   if (!running(s)) return;  // the same for every block of the row
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int St = a.g.stride;
   double val[1] = {0.0};
   if (i < a.g.vh) {
     const R al = (R)s->alpha;
-    Vec3<R> p = SpinorIO<S>::load(a.p + r * a.fb, St, i);
     Vec3<R> ap = SpinorIO<S>::load(a.ap + r * a.fb, St, i);
-    Vec3<R> rv = SpinorIO<S>::load(a.r + r * a.fb, St, i);
-    Vec3<typename SpinorIO<XP>::R> x = SpinorIO<XP>::load(a.xs + r * a.xs_fb, St, i);
     R n2 = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -54,18 +60,20 @@ __global__ void __launch_bounds__(256, 8) cg_update_kernel(VecArgs a) {
 
 // p = a r + beta p (a complex, 1 except right after a reliable update)
 template <int S>
-__global__ void __launch_bounds__(256, 8) cg_xpay_kernel(VecArgs a) {
-  griddep_launch_dependents();
-  griddep_wait();
+__global__ void __launch_bounds__(256, S == PREC_F64 ? 4 : 8) cg_xpay_kernel(VecArgs a) {
   using R = typename SpinorIO<S>::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
+  const int St = a.g.stride;
+  // p was last written at least two kernels back (r is the predecessor's)
+  Vec3<R> p;
+  if (i < a.g.vh) p = SpinorIO<S>::load(a.p + r * a.fb, St, i);
+  griddep_wait();
+  griddep_launch_dependents();
   const SlotState *s = a.slots + r;
   if (i >= a.g.vh || !running(s)) return;
-  const int St = a.g.stride;
   const R are = (R)s->a_re, aim = (R)s->a_im, beta = (R)s->beta;
   Vec3<R> rv = SpinorIO<S>::load(a.r + r * a.fb, St, i);
-  Vec3<R> p = SpinorIO<S>::load(a.p + r * a.fb, St, i);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     R px = fma(are, rv.c[c].x, fma(-aim, rv.c[c].y, beta * p.c[c].x));
@@ -81,9 +89,9 @@ __global__ void __launch_bounds__(256, 8) cg_xpay_kernel(VecArgs a) {
 // block: finish_init.  Slots already iterating are left alone, so systems
 // can join a running batch.
 template <int S>
-__global__ void __launch_bounds__(256, 8) cg_init_kernel(VecArgs a, int guess) {
-  griddep_launch_dependents();
+__global__ void __launch_bounds__(256, S == PREC_F64 ? 4 : 8) cg_init_kernel(VecArgs a, int guess) {
   griddep_wait();
+  griddep_launch_dependents();
   using R = typename SpinorIO<S>::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;

@@ -206,13 +206,13 @@ __device__ __forceinline__ Vec3<float> i16_vector(const uint4 q, float f) {
   return v;
 }
 
+// buf[0] holds direction 0's words on entry (loaded by the caller).
 template <int RECON, int NR>
 __device__ __forceinline__ void i16_hops(const DslashArgs &a, const SiteCoords &sc, int i, int r0,
-                                         const bool (&active)[NR], Vec3<float> (&acc)[NR]) {
+                                         const bool (&active)[NR], Vec3<float> (&acc)[NR],
+                                         I16Words<RECON> (&buf)[2]) {
   const Geom &g = a.g;
   const int S = g.stride;
-  I16Words<RECON> buf[2];
-  i16_load_words<RECON>(a.links, S, i, 0, buf[0]);
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
     if (mu < 3) i16_load_words<RECON>(a.links, S, i, mu + 1, buf[(mu + 1) & 1]);
@@ -298,6 +298,25 @@ __device__ __forceinline__ void many_rhs_hops(const DslashArgs &a, const SiteCoo
   }
 }
 
+// Direction 0's links of a site, loaded before the kernel waits for its
+// predecessor (links never change during a solve).  FP64 kernels do not
+// prefetch: the reliable-update pair is idle in most checkpoints, and would
+// stream a quarter of its links for nothing.
+template <int PREC, int RECON> struct FirstLinks {
+  static constexpr bool kUsed = (PREC == PREC_F32);
+  Mat3<typename AccumType<PREC>::R> m[4];
+  __device__ __forceinline__ void load(const DslashArgs &a, int i) {
+    LinkIO<PREC, RECON>::load(a.links, a.g.stride, i, 0, a.ls, m);
+  }
+};
+template <int RECON> struct FirstLinks<PREC_I16, RECON> {
+  static constexpr bool kUsed = true;
+  I16Words<RECON> buf[2];
+  __device__ __forceinline__ void load(const DslashArgs &a, int i) {
+    i16_load_words<RECON>(a.links, a.g.stride, i, 0, buf[0]);
+  }
+};
+
 // Launch bounds per precision: FP64 needs the large register file of the SM
 // (a 512-thread bound squeezes it to 64 registers and spills); FP32 and
 // 16-bit fit 128 registers at up to 512 threads.
@@ -310,14 +329,37 @@ dslash_kernel(const DslashArgs a) {
   using R = typename AccumType<PREC>::R;
   const Geom &g = a.g;
   const int S = g.stride;
-  griddep_launch_dependents();
-  griddep_wait();
   // Blocks of the RHS tiles of one range of sites are adjacent in the launch
   // order, so the tiles after the first find that range's links in L2.
   const int ntiles = (a.nrhs + NR - 1) / NR;
   const int tile = blockIdx.x % ntiles;
   const int i = (blockIdx.x / ntiles) * blockDim.x + threadIdx.x;
   const int r0 = tile * NR;
+
+  // Work that needs nothing from the predecessor kernel runs before waiting
+  // for it: direction 0's links (one-RHS and small tiles) and, for the m^2
+  // epilogue, the own-site p, which the kernel two launches back wrote (every
+  // kernel lets its successor launch only after its own wait, so that one
+  // has completed).
+  FirstLinks<PREC, RECON> first;
+  constexpr bool kFirst = FirstLinks<PREC, RECON>::kUsed && (PREC == PREC_I16 || NR < 8);
+  if constexpr (kFirst) {
+    if (i < g.vh) first.load(a, i);
+  }
+
+  constexpr bool kPreP = (MODE == MODE_MDAGM) && NR < 8;  // registers allow it
+  Vec3<R> pre[kPreP ? NR : 1];
+  if constexpr (kPreP) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (i < g.vh && r0 + r < a.nrhs)
+        pre[r] = SpinorIO<PREC>::load(a.p + (size_t)(r0 + r) * a.p_fb, S, i);
+      else
+        zero(pre[r]);
+    }
+  }
+  griddep_wait();
+  griddep_launch_dependents();
 
   // Gate: the decision is the same in every block of a tile row (a system's
   // state only changes in the warp that completes a reduction over its row,
@@ -342,29 +384,17 @@ dslash_kernel(const DslashArgs a) {
 #pragma unroll
   for (int r = 0; r < NR; ++r) zero(acc[r]);
 
-  // the epilogue's own-site operand is fetched up front so its latency hides
-  // behind the link stream
-  constexpr bool kPreP = (MODE == MODE_MDAGM) && NR < 8;  // registers allow it
-  Vec3<R> pre[kPreP ? NR : 1];
-  if constexpr (kPreP) {
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      if (valid && active[r]) pre[r] = SpinorIO<PREC>::load(a.p + (size_t)(r0 + r) * a.p_fb, S, i);
-      else zero(pre[r]);
-    }
-  }
-
   if (valid) {
     const SiteCoords sc = site_coords(g, a.out_parity, i);
     if constexpr (PREC == PREC_I16) {
-      i16_hops<RECON, NR>(a, sc, i, r0, active, acc);
+      i16_hops<RECON, NR>(a, sc, i, r0, active, acc, first.buf);
     } else if constexpr (PREC == PREC_F32 && NR >= 8) {
       many_rhs_hops<RECON, NR>(a, sc, i, r0, active, acc);
     } else {
 #pragma unroll 1
       for (int mu = 0; mu < 4; ++mu) {
-        Mat3<R> m[4];
-        LinkIO<PREC, RECON>::load(a.links, S, i, mu, a.ls, m);
+        Mat3<R>(&m)[4] = first.m;  // direction 0 arrived before the wait
+        if (!kFirst || mu > 0) LinkIO<PREC, RECON>::load(a.links, S, i, mu, a.ls, m);
         float sg[4];
         int nb[4];
         nb[0] = hop_index(g, sc, mu, +1, sg[0]);
