@@ -40,7 +40,7 @@ CG_FLOPS_PER_SITE_ITER = 2364
 PAPER_CONTEXT_GFLOPS = 46.48   # mixed-precision CG, GTX Titan Black (Table 2)
 # DRAM traffic of one FP32 18-real Dslash launch at 20^3 x 64 from an ncu
 # capture of the kernel source with this fingerprint (None: not captured).
-NCU_TRAFFIC = {'fingerprint': '0b746fefc82a2abf', 'bytes_per_launch': 306.3e6}
+NCU_TRAFFIC = {'fingerprint': '2aba04019599587a', 'bytes_per_launch': 306.2e6}
 
 
 def parse_args():
@@ -366,6 +366,11 @@ def full_lattice_workload(ctx, sq, stream, fat, lng):
     f, l = torch.empty_like(thin), torch.empty_like(thin)
     ctx.gauge_fatten(dims, thin, f, l, stream=stream)
     ms_f, _ = timed(lambda: ctx.gauge_fatten(dims, thin, f, l, stream=stream), stream, 5)
+    ctx.gauge_fatten_asqtad(dims, thin, f, l, stream=stream)
+    ms_a, _ = timed(lambda: ctx.gauge_fatten_asqtad(dims, thin, f, l, stream=stream), stream, 2)
+    # asqtad: 6 x 2 + 24 x 4 + 48 x 6 + 6 x 4 products for the fat link, 2
+    # for the Naik link (216 flops each), 85 scaled adds of 18 reals
+    flops_a = 4 * vol * (422 * 216 + 85 * 36)
     # flops per link: 6 staples x 2 products + Naik 2 products, 3x3 complex
     # product = 27 complex multiply-adds = 216 real flops; plus the sums
     flops = 4 * vol * (14 * 216 + 6 * 18 + 36)
@@ -376,6 +381,13 @@ def full_lattice_workload(ctx, sq, stream, fat, lng):
                                   'odd sites reconstructed',
                       'ms': round(ms, 3), 'iterations': st['iterations'],
                       'full_true_residual': st['true_residual']},
+            'fatten_asqtad': {'workload': '20^3x64 thin links (eps 0.25, seed 0) -> asqtad fat '
+                                          'links (MILC path set: 1-link, 6 3-link, 24 5-link, '
+                                          '48 7-link staples, 6 Lepage) and Naik links, FP64',
+                              'ms': round(ms_a, 3),
+                              'gflops_fp64': round(flops_a / (ms_a * 1e-3) / 1e9, 1),
+                              'frac_of_fp64_peak': round(flops_a / (ms_a * 1e-3) / 1e12 / peak,
+                                                         4)},
             'fatten': {'workload': '20^3x64 thin links (eps 0.25, seed 0) -> fat (6 staples) and '
                                    'long links, FP64',
                        'ms': round(ms_f, 3), 'gflops_fp64': round(gfl, 1),

@@ -157,6 +157,22 @@ int gauge_free(sq_ctx *ctx, int gauge_id);
 int gauge_fatten(sq_ctx *ctx, const int dims[4], const double *thin_dev, double c1, double c3,
                  double staple_weight, double *fat_dev, double *lng_dev, void *stream);
 
+/* The asqtad action's fat and Naik links from thin links, on the device in
+ * FP64: MILC's path set for the fat link -- the one-link term, the 6
+ * three-link, 24 five-link and 48 seven-link staples and the 6 Lepage terms
+ * of direction mu, each the product of links along its path -- and the Naik
+ * link c_N U_mu(x) U_mu(x+mu) U_mu(x+2mu).  coeffs = {one-link, 3-staple,
+ * 5-staple, 7-staple, Lepage, Naik}; with the paths oriented as
+ *   (s nu) mu (-s nu),  (r rho)(s nu) mu (-s nu)(-r rho),  ...,
+ *   (s nu)(s nu) mu (-s nu)(-s nu)
+ * (a hop +d at y multiplies by U_d(y), a hop -d by U_d(y-d)^dag), the
+ * tree-level asqtad values are {5/8, 1/16, 1/64, 1/384, -1/16, -1/24}, which
+ * give 9/8 and -1/24 on unit links.  The paper's lattices are MILC asqtad
+ * ensembles (Sec. 2, Fig. 1).  Arrays as for gauge_fatten; asynchronous on
+ * `stream`. */
+int gauge_fatten_asqtad(sq_ctx *ctx, const int dims[4], const double *thin_dev,
+                        const double coeffs[6], double *fat_dev, double *lng_dev, void *stream);
+
 /* gauge_fatten followed by gauge_load: thin links in (host pointer, or device
  * with SQ_GAUGE_DEVICE_PTRS), a gauge id out.  The fat and long links exist
  * on the device only transiently (staging outside the HBM budget, freed on

@@ -69,6 +69,7 @@ def _load():
             lib.oracle_quantize_spinor_i16.argtypes = [Lg, P, P, P]
             lib.oracle_quantize_links_i16.argtypes = [Lg, P, D, P]
             lib.oracle_fat_long.argtypes = [P, P, D, D, D, P, P]
+            lib.oracle_asqtad_links.argtypes = [P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -206,6 +207,25 @@ def fat_long(dims, thin, c1=C1, c3=C3, w=STAPLE_WEIGHT):
     lng = np.zeros_like(u)
     lib.oracle_fat_long(_ptr(_dims(dims)), _ptr(u), float(c1), float(c3), float(w), _ptr(fat),
                         _ptr(lng))
+    return fat, lng
+
+
+# Tree-level asqtad path coefficients with the orientation of oracle.c:
+# one-link, 3-staple, 5-staple, 7-staple, Lepage, Naik.
+ASQTAD_COEFFS = (5.0 / 8.0, 1.0 / 16.0, 1.0 / 64.0, 1.0 / 384.0, -1.0 / 16.0, -1.0 / 24.0)
+
+
+def asqtad_links(dims, thin, coeffs=ASQTAD_COEFFS):
+    """Fat and Naik links of the asqtad action (MILC's path set: one-link,
+    3-, 5- and 7-link staples, Lepage term) from thin links -- the kind of
+    links the paper's MILC lattices carry (Sec. 2).  See oracle.c."""
+    lib = _load()
+    u = _c128(thin)
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    assert c.shape == (6,)
+    fat = np.zeros_like(u)
+    lng = np.zeros_like(u)
+    lib.oracle_asqtad_links(_ptr(_dims(dims)), _ptr(u), _ptr(c), _ptr(fat), _ptr(lng))
     return fat, lng
 
 

@@ -500,3 +500,99 @@ void oracle_fat_long(const int L[4], const double *u, double c1, double c3, doub
         }
     }
 }
+
+/* ------------------------------------------------- asqtad fat links (MILC form)
+ * The asqtad action's fat link, tree-level coefficients with the paths
+ * oriented as below: one-link c1 = 5/8, 3-staple c3 = 1/16, 5-staple
+ * c5 = 1/64, 7-staple c7 = 1/384, Lepage cL = -1/16 (unit links give
+ * c1 + 6 c3 + 24 c5 + 48 c7 + 6 cL = 9/8); the Naik link is cN U U U with
+ * cN = -1/24.  For direction mu, a staple of the mu-directed field W in
+ * direction nu with sign s is
+ *   s = +1:  U_nu(x) W(x+nu) U_nu(x+mu)^dag,
+ *   s = -1:  U_nu(x-nu)^dag W(x-nu) U_nu(x-nu+mu),
+ * and
+ *   P3[nu,s]             = staple(U_mu; nu, s),
+ *   P5[nu,s][rho,r]      = staple(P3[nu,s]; rho, r),          rho != mu, nu,
+ *   P7[nu,s][rho,r][sg,q] = staple(P5[nu,s][rho,r]; sg, q),  sg != mu, nu, rho,
+ *   Lepage[nu,s]         = staple(P3[nu,s]; nu, s),
+ *   F_mu = c1 U_mu + c3 sum P3 + c5 sum P5 + c7 sum P7 + cL sum Lepage,
+ * every sum over all directions and signs allowed.  Whole-lattice fields of
+ * 3x3 matrices, built one staple at a time. */
+
+static void staple_field(const int L[4], const double *u, int mu, int nu, int s,
+                         const cplx *w, cplx *out)
+{
+    long vol = oracle_volume(L);
+    #pragma omp parallel for schedule(static)
+    for (long x = 0; x < vol; x++) {
+        cplx t[9];
+        if (s > 0) {
+            long xpn = oracle_neighbor(L, x, nu, 1, 1, NULL);
+            long xpm = oracle_neighbor(L, x, mu, 1, 1, NULL);
+            mat_mul(t, link_at(u, x, nu), w + 9 * xpn, 0, 0);
+            mat_mul(out + 9 * x, t, link_at(u, xpm, nu), 0, 1);
+        } else {
+            long xmn = oracle_neighbor(L, x, nu, -1, 1, NULL);
+            long xmnpm = oracle_neighbor(L, xmn, mu, 1, 1, NULL);
+            mat_mul(t, link_at(u, xmn, nu), w + 9 * xmn, 1, 0);
+            mat_mul(out + 9 * x, t, link_at(u, xmnpm, nu), 0, 0);
+        }
+    }
+}
+
+static void add_field(long n, cplx *acc, double c, const cplx *a)
+{
+    #pragma omp parallel for schedule(static)
+    for (long k = 0; k < n; k++) acc[k] += c * a[k];
+}
+
+void oracle_asqtad_links(const int L[4], const double *u, const double coef[6], double *fat,
+                         double *lng)
+{
+    const double c1 = coef[0], c3 = coef[1], c5 = coef[2], c7 = coef[3], cl = coef[4],
+                 cn = coef[5];
+    long vol = oracle_volume(L), n = 9 * vol;
+    cplx *umu = malloc(sizeof(cplx) * n), *acc = malloc(sizeof(cplx) * n);
+    cplx *p3 = malloc(sizeof(cplx) * n), *p5 = malloc(sizeof(cplx) * n);
+    cplx *p7 = malloc(sizeof(cplx) * n), *lp = malloc(sizeof(cplx) * n);
+    for (int mu = 0; mu < 4; mu++) {
+        for (long x = 0; x < vol; x++)
+            for (int e = 0; e < 9; e++) umu[9 * x + e] = link_at(u, x, mu)[e];
+        for (long k = 0; k < n; k++) acc[k] = c1 * umu[k];
+        for (int nu = 0; nu < 4; nu++) {
+            if (nu == mu) continue;
+            for (int s = -1; s <= 1; s += 2) {
+                staple_field(L, u, mu, nu, s, umu, p3);
+                add_field(n, acc, c3, p3);
+                staple_field(L, u, mu, nu, s, p3, lp);
+                add_field(n, acc, cl, lp);
+                for (int rho = 0; rho < 4; rho++) {
+                    if (rho == mu || rho == nu) continue;
+                    for (int r = -1; r <= 1; r += 2) {
+                        staple_field(L, u, mu, rho, r, p3, p5);
+                        add_field(n, acc, c5, p5);
+                        for (int sg = 0; sg < 4; sg++) {
+                            if (sg == mu || sg == nu || sg == rho) continue;
+                            for (int q = -1; q <= 1; q += 2) {
+                                staple_field(L, u, mu, sg, q, p5, p7);
+                                add_field(n, acc, c7, p7);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        for (long x = 0; x < vol; x++) {
+            cplx *f = (cplx *)(fat + ((x * 4 + mu) * 9) * 2);
+            for (int e = 0; e < 9; e++) f[e] = acc[9 * x + e];
+            cplx t[9];
+            long xpm = oracle_neighbor(L, x, mu, 1, 1, NULL);
+            long xp2m = oracle_neighbor(L, x, mu, 2, 1, NULL);
+            mat_mul(t, link_at(u, x, mu), link_at(u, xpm, mu), 0, 0);
+            cplx *l = (cplx *)(lng + ((x * 4 + mu) * 9) * 2);
+            mat_mul(l, t, link_at(u, xp2m, mu), 0, 0);
+            for (int e = 0; e < 9; e++) l[e] *= cn;
+        }
+    }
+    free(umu); free(acc); free(p3); free(p5); free(p7); free(lp);
+}

@@ -125,6 +125,136 @@ __global__ void __launch_bounds__(128) fatten_kernel(FatGeom g, const double2 *u
   for (int e = 0; e < 9; ++e) l[e] = make_double2(c3 * n.e[e].x, c3 * n.e[e].y);
 }
 
+// ---------------------------------------------------------------- asqtad
+// The asqtad action's fat link (MILC's path set): the one-link term, the 6
+// three-link staples, 24 five-link and 48 seven-link staples and 6 Lepage
+// terms, each a product of links along its path, weighted by its
+// coefficient; the Naik link is c_N U U U.  Paths, for direction mu, with
+// nu, rho, sigma distinct and != mu and every sign s, r, q = +-1:
+//   3-staple  (s nu) mu (-s nu)
+//   5-staple  (r rho)(s nu) mu (-s nu)(-r rho)
+//   7-staple  (q sg)(r rho)(s nu) mu (-s nu)(-r rho)(-q sg)
+//   Lepage    (s nu)(s nu) mu (-s nu)(-s nu)
+// A hop +d at y multiplies by U_d(y), a hop -d by U_d(y - d)^dag.  One thread
+// per (site, direction) walks every path; about 420 SU(3) products a link.
+
+struct Walker {
+  const FatGeom &g;
+  const double2 *u;
+  int c[4];
+  long pos;
+  __device__ Walker(const FatGeom &g_, const double2 *u_, const int c0[4], long x)
+      : g(g_), u(u_), pos(x) {
+    for (int k = 0; k < 4; ++k) c[k] = c0[k];
+  }
+  __device__ __forceinline__ void move(int d, int s) {
+    int v = c[d] + s;
+    v = (v < 0) ? v + g.L[d] : (v >= g.L[d] ? v - g.L[d] : v);
+    pos += (long)(v - c[d]) * g.st[d];
+    c[d] = v;
+  }
+  // the link matrix of hop (d, s) from the current position; moves
+  __device__ __forceinline__ M3 hop(int d, int s) {
+    if (s > 0) {
+      const M3 l = load_link(u, pos, d);
+      move(d, 1);
+      return l;
+    }
+    move(d, -1);
+    const M3 l = load_link(u, pos, d);
+    M3 t;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) t.e[3 * i + j] = cconj(l.e[3 * j + i]);
+    return t;
+  }
+};
+
+// Product along a path of n hops (dirs/signs) starting at site x.
+__device__ M3 path_product(const FatGeom &g, const double2 *u, const int c0[4], long x,
+                           const int *dirs, const int *signs, int n) {
+  Walker w(g, u, c0, x);
+  M3 m = w.hop(dirs[0], signs[0]);
+  for (int k = 1; k < n; ++k) m = mul<false, false>(m, w.hop(dirs[k], signs[k]));
+  return m;
+}
+
+__device__ __forceinline__ void add_scaled(M3 &acc, double c, const M3 &m) {
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    acc.e[e].x = fma(c, m.e[e].x, acc.e[e].x);
+    acc.e[e].y = fma(c, m.e[e].y, acc.e[e].y);
+  }
+}
+
+struct AsqtadCoeffs {
+  double one, three, five, seven, lepage, naik;
+};
+
+__global__ void __launch_bounds__(128) asqtad_kernel(FatGeom g, const double2 *u, AsqtadCoeffs k,
+                                                     double2 *fat, double2 *lng) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 4 * g.vol) return;
+  const long x = idx >> 2;
+  const int mu = (int)(idx & 3);
+  int c[4];
+  {
+    long r = x;
+    c[0] = (int)(r % g.L[0]); r /= g.L[0];
+    c[1] = (int)(r % g.L[1]); r /= g.L[1];
+    c[2] = (int)(r % g.L[2]);
+    c[3] = (int)(r / g.L[2]);
+  }
+  M3 acc;
+  {
+    const M3 l = load_link(u, x, mu);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) acc.e[e] = make_double2(k.one * l.e[e].x, k.one * l.e[e].y);
+  }
+  int dirs[7], signs[7];
+#pragma unroll 1
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu) continue;
+#pragma unroll 1
+    for (int s = -1; s <= 1; s += 2) {
+      // 3-staple and Lepage
+      dirs[0] = nu; signs[0] = s; dirs[1] = mu; signs[1] = 1; dirs[2] = nu; signs[2] = -s;
+      add_scaled(acc, k.three, path_product(g, u, c, x, dirs, signs, 3));
+      dirs[0] = nu; signs[0] = s; dirs[1] = nu; signs[1] = s; dirs[2] = mu; signs[2] = 1;
+      dirs[3] = nu; signs[3] = -s; dirs[4] = nu; signs[4] = -s;
+      add_scaled(acc, k.lepage, path_product(g, u, c, x, dirs, signs, 5));
+#pragma unroll 1
+      for (int rho = 0; rho < 4; ++rho) {
+        if (rho == mu || rho == nu) continue;
+#pragma unroll 1
+        for (int r = -1; r <= 1; r += 2) {
+          dirs[0] = rho; signs[0] = r; dirs[1] = nu; signs[1] = s; dirs[2] = mu; signs[2] = 1;
+          dirs[3] = nu; signs[3] = -s; dirs[4] = rho; signs[4] = -r;
+          add_scaled(acc, k.five, path_product(g, u, c, x, dirs, signs, 5));
+          const int sg = 6 - mu - nu - rho;  // the fourth direction
+#pragma unroll 1
+          for (int q = -1; q <= 1; q += 2) {
+            dirs[0] = sg; signs[0] = q; dirs[1] = rho; signs[1] = r; dirs[2] = nu; signs[2] = s;
+            dirs[3] = mu; signs[3] = 1; dirs[4] = nu; signs[4] = -s; dirs[5] = rho;
+            signs[5] = -r; dirs[6] = sg; signs[6] = -q;
+            add_scaled(acc, k.seven, path_product(g, u, c, x, dirs, signs, 7));
+          }
+        }
+      }
+    }
+  }
+  double2 *f = fat + idx * 9;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) f[e] = acc.e[e];
+  dirs[0] = dirs[1] = dirs[2] = mu;
+  signs[0] = signs[1] = signs[2] = 1;
+  const M3 n = path_product(g, u, c, x, dirs, signs, 3);
+  double2 *l = lng + idx * 9;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) l[e] = make_double2(k.naik * n.e[e].x, k.naik * n.e[e].y);
+}
+
 int check_dims(const int dims[4], long *vol) {
   long v = 1;
   for (int mu = 0; mu < 4; ++mu) {
@@ -153,10 +283,42 @@ int launch_fatten(const int dims[4], long vol, const double *thin, double c1, do
   return SQ_OK;
 }
 
+FatGeom make_fat_geom(const int dims[4], long vol) {
+  FatGeom g;
+  for (int mu = 0; mu < 4; ++mu) g.L[mu] = dims[mu];
+  g.st[0] = 1;
+  g.st[1] = dims[0];
+  g.st[2] = (long)dims[0] * dims[1];
+  g.st[3] = (long)dims[0] * dims[1] * dims[2];
+  g.vol = vol;
+  return g;
+}
+
 }  // namespace
 }  // namespace sq
 
 using namespace sq;
+
+extern "C" int gauge_fatten_asqtad(sq_ctx *ctx, const int dims[4], const double *thin_dev,
+                                   const double coeffs[6], double *fat_dev, double *lng_dev,
+                                   void *stream) {
+  if (!ctx || !dims || !thin_dev || !coeffs || !fat_dev || !lng_dev) return SQ_ERR_ARG;
+  for (int k = 0; k < 6; ++k)
+    if (!std::isfinite(coeffs[k])) return SQ_ERR_ARG;
+  long vol;
+  int rc = check_dims(dims, &vol);
+  if (rc) return rc;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  const AsqtadCoeffs k{coeffs[0], coeffs[1], coeffs[2], coeffs[3], coeffs[4], coeffs[5]};
+  const long n = 4 * vol;
+  asqtad_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+      make_fat_geom(dims, vol), reinterpret_cast<const double2 *>(thin_dev), k,
+      reinterpret_cast<double2 *>(fat_dev), reinterpret_cast<double2 *>(lng_dev));
+  SQ_CUDA_TRY(cudaGetLastError());
+  ctx->launches++;
+  return SQ_OK;
+}
 
 extern "C" int gauge_fatten(sq_ctx *ctx, const int dims[4], const double *thin_dev, double c1,
                             double c3, double staple_weight, double *fat_dev, double *lng_dev,

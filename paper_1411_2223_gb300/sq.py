@@ -84,6 +84,7 @@ SIGNATURES = {
     'gauge_free': (_I, [_P, _I]),
     'gauge_fatten': (_I, [_P, _P, _P, _D, _D, _D, _P, _P, _P]),
     'gauge_load_thin': (_I, [_P, _P, _P, _D, _D, _D, _U, ctypes.POINTER(_I)]),
+    'gauge_fatten_asqtad': (_I, [_P, _P, _P, _P, _P, _P, _P]),
     'sq_spinor_bytes': (_I, [_P, _I, _I, ctypes.POINTER(_SZ), ctypes.POINTER(_I)]),
     'sq_pack_spinor': (_I, [_P, _I, _I, _P, _P, _P]),
     'sq_unpack_spinor': (_I, [_P, _I, _I, _P, _P, _P]),
@@ -215,6 +216,18 @@ class Context:
         _check(self._lib.gauge_fatten(self.handle, d, _ptr(thin_dev), float(c1), float(c3),
                                       float(staple_weight), _ptr(fat_dev), _ptr(lng_dev),
                                       _stream(stream)), 'gauge_fatten')
+
+    ASQTAD_COEFFS = (5.0 / 8.0, 1.0 / 16.0, 1.0 / 64.0, 1.0 / 384.0, -1.0 / 16.0, -1.0 / 24.0)
+
+    def gauge_fatten_asqtad(self, dims, thin_dev, fat_dev, lng_dev, coeffs=ASQTAD_COEFFS,
+                            stream=None):
+        """asqtad fat (MILC path set) and Naik links from thin links on the
+        device (torch CUDA tensors of shape (V, 4, 3, 3) complex128)."""
+        d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+        c = (ctypes.c_double * 6)(*[float(v) for v in coeffs])
+        _check(self._lib.gauge_fatten_asqtad(self.handle, d, _ptr(thin_dev), c, _ptr(fat_dev),
+                                             _ptr(lng_dev), _stream(stream)),
+               'gauge_fatten_asqtad')
 
     def gauge_load_thin(self, dims, thin, c1=9.0 / 8.0, c3=-1.0 / 24.0, staple_weight=0.1,
                         antiperiodic_t=False, flags=0):
@@ -435,7 +448,7 @@ def _forward(name):
     return f
 
 
-for _n in ('gauge_load', 'gauge_free', 'gauge_fatten', 'gauge_load_thin', 'dslash_apply', 'mdagm_apply', 'cg_solve',
+for _n in ('gauge_load', 'gauge_free', 'gauge_fatten', 'gauge_load_thin', 'gauge_fatten_asqtad', 'dslash_apply', 'mdagm_apply', 'cg_solve',
            'cg_solve_multi', 'cg_solve_multishift', 'cg_solve_full', 'dirac_apply',
            'serve_submit', 'serve_poll',
            'serve_cancel', 'serve_stats', 'serve_configure'):

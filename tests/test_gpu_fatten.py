@@ -74,3 +74,50 @@ def test_fatten_full_size_20x64(sq):
     f0, l0 = oracle.fat_long(dims, thin)
     assert np.abs(fat - f0).max() <= 1e-14
     assert np.abs(lng - l0).max() <= 1e-15
+
+
+def _asqtad_gpu(sq, dims, thin):
+    import torch
+    u = torch.from_numpy(np.ascontiguousarray(thin)).cuda()
+    fat = torch.zeros_like(u)
+    lng = torch.zeros_like(u)
+    sq.gauge_fatten_asqtad(dims, u, fat, lng)
+    torch.cuda.synchronize()
+    return fat, lng
+
+
+@pytest.mark.parametrize('dims', [(4, 6, 8, 10), (2, 4, 6, 4)])
+def test_asqtad_links_match_oracle(sq, dims):
+    thin = synth.thin_links(dims, 0.6, seed=4)
+    fat, lng = _asqtad_gpu(sq, dims, thin)
+    f0, l0 = oracle.asqtad_links(dims, thin)
+    assert np.abs(fat.cpu().numpy() - f0).max() <= 1e-14
+    assert np.abs(lng.cpu().numpy() - l0).max() <= 1e-15
+
+
+def test_asqtad_links_solve(sq):
+    """A CG solve on the GPU-built asqtad links (12-real Naik links) meets the
+    oracle's residual computed on the oracle's own asqtad links."""
+    dims = (4, 6, 8, 10)
+    thin = synth.thin_links(dims, 0.25, seed=0)
+    fat_d, lng_d = _asqtad_gpu(sq, dims, thin)
+    f0, l0 = oracle.asqtad_links(dims, thin)
+    gid = sq.gauge_load(dims, fat_d, lng_d)
+    try:
+        b = synth.gaussian_source(oracle.volume(dims) // 2, 2)
+        for prec, recon in (('f32', 12), ('i16', 12), ('f64', 18)):
+            x, st = sq.cg_solve(gid, b, 0.03, 1e-9, precision=prec, long_recon=recon)
+            assert st['status'] == 0
+            assert oracle.true_residual(dims, f0, l0, 0.03, b, x) <= 1e-9
+    finally:
+        sq.gauge_free(gid)
+
+
+def test_asqtad_full_size_20x64(sq):
+    """The benchmark lattice 20^3 x 64: every asqtad link against the oracle."""
+    dims = (20, 20, 20, 64)
+    thin = synth.thin_links(dims, 0.25, seed=0)
+    fat, lng = _asqtad_gpu(sq, dims, thin)
+    f0, l0 = oracle.asqtad_links(dims, thin)
+    assert np.abs(fat.cpu().numpy() - f0).max() <= 1e-14
+    assert np.abs(lng.cpu().numpy() - l0).max() <= 1e-15
