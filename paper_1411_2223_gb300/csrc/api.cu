@@ -28,6 +28,7 @@ void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int 
 
 LinkScales GaugeField::scales(int prec, int recon) const {
   LinkScales s;
+  s.keep = 0;
   s.fat_k = fat_scale / 32767.f;
   s.long_k = long_scale / 32767.f;
   s.recon_d = (long_s != 0) ? 1.0 / long_s : 0.0;

@@ -154,11 +154,11 @@ __device__ __forceinline__ void put4(uint32_t *w, uint4 q) {
 
 template <int RECON>
 __device__ __forceinline__ void i16_load_words(const char *links, int S, int i, int mu,
-                                               I16Words<RECON> &d) {
+                                               I16Words<RECON> &d, bool keep) {
   using LL = LinkLayout<PREC_I16, RECON>;
   const char *fat = links + (size_t)mu * LL::mu_bytes * S;
   const char *lng = fat + (size_t)LL::fat_bytes * S;
-  const uint64_t pol = l2_evict_first_policy();
+  const uint64_t pol = l2_link_policy(keep);
 #pragma unroll
   for (int k = 0; k < 4; ++k) put4(d.w + 4 * k, ld_stream_u4(fat + ((size_t)k * S + i) * 16, pol));
   {
@@ -208,14 +208,15 @@ __device__ __forceinline__ Vec3<float> i16_vector(const uint4 q, float f) {
 
 // buf[0] holds direction 0's words on entry (loaded by the caller).
 template <int RECON, int NR>
-__device__ __forceinline__ void i16_hops(const DslashArgs &a, const SiteCoords &sc, int i, int r0,
+__device__ __forceinline__ void i16_hops(const DslashArgs &a, const LinkScales &ls,
+                                         const SiteCoords &sc, int i, int r0,
                                          const bool (&active)[NR], Vec3<float> (&acc)[NR],
                                          I16Words<RECON> (&buf)[2]) {
   const Geom &g = a.g;
   const int S = g.stride;
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
-    if (mu < 3) i16_load_words<RECON>(a.links, S, i, mu + 1, buf[(mu + 1) & 1]);
+    if (mu < 3) i16_load_words<RECON>(a.links, S, i, mu + 1, buf[(mu + 1) & 1], ls.keep);
     const uint32_t *w = buf[mu & 1].w;
     int nb[4];
     float f[4];
@@ -224,7 +225,7 @@ __device__ __forceinline__ void i16_hops(const DslashArgs &a, const SiteCoords &
     nb[2] = hop<+3>(g, sc, mu, f[2]);
     nb[3] = hop<-3>(g, sc, mu, f[3]);
     const float eta = eta_sign(sc, mu);
-    const float kf = eta * a.ls.fat_k, kl = eta * a.ls.long_k;
+    const float kf = eta * ls.fat_k, kl = eta * ls.long_k;
     f[0] *= kf;
     f[1] *= -kf;
     f[2] *= kl;
@@ -247,7 +248,7 @@ __device__ __forceinline__ void i16_hops(const DslashArgs &a, const SiteCoords &
           Mat3<float> m;
 #pragma unroll
           for (int e = 0; e < 6; ++e) m.e[e] = decode_word(w[18 + 6 * h + e]);
-          reconstruct_row2(m, a.ls.recon_f);
+          reconstruct_row2(m, ls.recon_f);
           mat_vec_acc(acc[r], m, i16_vector(q[2 + h], f[2 + h]));
         }
       }
@@ -261,9 +262,9 @@ __device__ __forceinline__ void i16_hops(const DslashArgs &a, const SiteCoords &
 // matrices is held at a time and applied to every system, with the hop's
 // sign (eta, backward hop, antiperiodic wrap) folded into the gathered vector.
 template <int RECON, int NR>
-__device__ __forceinline__ void many_rhs_hops(const DslashArgs &a, const SiteCoords &sc, int i,
-                                              int r0, const bool (&active)[NR],
-                                              Vec3<float> (&acc)[NR]) {
+__device__ __forceinline__ void many_rhs_hops(const DslashArgs &a, const LinkScales &ls,
+                                              const SiteCoords &sc, int i, int r0,
+                                              const bool (&active)[NR], Vec3<float> (&acc)[NR]) {
   const Geom &g = a.g;
   const int S = g.stride;
 #pragma unroll 1
@@ -282,8 +283,8 @@ __device__ __forceinline__ void many_rhs_hops(const DslashArgs &a, const SiteCoo
 #pragma unroll
     for (int kind = 0; kind < 2; ++kind) {
       Mat3<float> m[2];
-      if (kind == 0) LinkIO<PREC_F32, RECON>::template load_pair<0>(a.links, S, i, mu, a.ls, m);
-      else LinkIO<PREC_F32, RECON>::template load_pair<1>(a.links, S, i, mu, a.ls, m);
+      if (kind == 0) LinkIO<PREC_F32, RECON>::template load_pair<0>(a.links, S, i, mu, ls, m);
+      else LinkIO<PREC_F32, RECON>::template load_pair<1>(a.links, S, i, mu, ls, m);
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         if (!active[r]) continue;
@@ -305,15 +306,15 @@ __device__ __forceinline__ void many_rhs_hops(const DslashArgs &a, const SiteCoo
 template <int PREC, int RECON> struct FirstLinks {
   static constexpr bool kUsed = (PREC == PREC_F32);
   Mat3<typename AccumType<PREC>::R> m[4];
-  __device__ __forceinline__ void load(const DslashArgs &a, int i) {
-    LinkIO<PREC, RECON>::load(a.links, a.g.stride, i, 0, a.ls, m);
+  __device__ __forceinline__ void load(const DslashArgs &a, const LinkScales &ls, int i) {
+    LinkIO<PREC, RECON>::load(a.links, a.g.stride, i, 0, ls, m);
   }
 };
 template <int RECON> struct FirstLinks<PREC_I16, RECON> {
   static constexpr bool kUsed = true;
   I16Words<RECON> buf[2];
-  __device__ __forceinline__ void load(const DslashArgs &a, int i) {
-    i16_load_words<RECON>(a.links, a.g.stride, i, 0, buf[0]);
+  __device__ __forceinline__ void load(const DslashArgs &a, const LinkScales &ls, int i) {
+    i16_load_words<RECON>(a.links, a.g.stride, i, 0, buf[0], ls.keep);
   }
 };
 
@@ -335,6 +336,8 @@ dslash_kernel(const DslashArgs a) {
   const int tile = blockIdx.x % ntiles;
   const int i = (blockIdx.x / ntiles) * blockDim.x + threadIdx.x;
   const int r0 = tile * NR;
+  LinkScales ls = a.ls;
+  ls.keep = tile < ntiles - 1;  // a later tile of this site range reads the links again
 
   // Work that needs nothing from the predecessor kernel runs before waiting
   // for it: direction 0's links (one-RHS and small tiles) and, for the m^2
@@ -344,7 +347,7 @@ dslash_kernel(const DslashArgs a) {
   FirstLinks<PREC, RECON> first;
   constexpr bool kFirst = FirstLinks<PREC, RECON>::kUsed && (PREC == PREC_I16 || NR < 8);
   if constexpr (kFirst) {
-    if (i < g.vh) first.load(a, i);
+    if (i < g.vh) first.load(a, ls, i);
   }
 
   constexpr bool kPreP = (MODE == MODE_MDAGM) && NR < 8;  // registers allow it
@@ -387,14 +390,14 @@ dslash_kernel(const DslashArgs a) {
   if (valid) {
     const SiteCoords sc = site_coords(g, a.out_parity, i);
     if constexpr (PREC == PREC_I16) {
-      i16_hops<RECON, NR>(a, sc, i, r0, active, acc, first.buf);
+      i16_hops<RECON, NR>(a, ls, sc, i, r0, active, acc, first.buf);
     } else if constexpr (PREC == PREC_F32 && NR >= 8) {
-      many_rhs_hops<RECON, NR>(a, sc, i, r0, active, acc);
+      many_rhs_hops<RECON, NR>(a, ls, sc, i, r0, active, acc);
     } else {
 #pragma unroll 1
       for (int mu = 0; mu < 4; ++mu) {
         Mat3<R>(&m)[4] = first.m;  // direction 0 arrived before the wait
-        if (!kFirst || mu > 0) LinkIO<PREC, RECON>::load(a.links, S, i, mu, a.ls, m);
+        if (!kFirst || mu > 0) LinkIO<PREC, RECON>::load(a.links, S, i, mu, ls, m);
         float sg[4];
         int nb[4];
         nb[0] = hop_index(g, sc, mu, +1, sg[0]);

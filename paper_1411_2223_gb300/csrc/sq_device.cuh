@@ -148,9 +148,13 @@ __device__ __forceinline__ void reconstruct_row2(Mat3<R> &m, R f) {
 // in L2).  Colour vectors are gathered 16 times per site: let them allocate
 // in L1.
 
-__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+// keep = true: another tile of the same launch reads these links again soon
+// (its blocks are adjacent in the launch order), so they stay evict-normal;
+// the last reader marks them evict-first.
+__device__ __forceinline__ uint64_t l2_link_policy(bool keep) {
   uint64_t p;
-  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  if (keep) asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  else asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
 
@@ -328,6 +332,7 @@ struct LinkScales {
   float long_k;     // I16: value = code * long_k
   float recon_f;    // 12-real: row2 = recon_f * conj(row0 x row1) in stored units
   double recon_d;   // same, FP64 kernels
+  int keep;         // set in the kernel: links read again by a later tile
 };
 
 // Loader of the four hop matrices of direction mu at site i.
@@ -339,7 +344,7 @@ template <int RECON> struct LinkIO<PREC_F64, RECON> {
                                               const LinkScales &ls, Mat3<double> m[4]) {
     const char *fat = links + (size_t)mu * LL::mu_bytes * S;
     const char *lng = fat + (size_t)LL::fat_bytes * S;
-    const uint64_t pol = l2_evict_first_policy();
+    const uint64_t pol = l2_link_policy(ls.keep);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       m[0].e[k] = ld_stream_d2(fat + ((size_t)k * S + i) * 16, pol);
@@ -374,7 +379,7 @@ template <int RECON> struct LinkIO<PREC_F32, RECON> {
                                                    const LinkScales &ls, Mat3<float> m[2]) {
     const char *base = links + (size_t)mu * LL::mu_bytes * S;
     if (KIND == 1) base += (size_t)LL::fat_bytes * S;
-    const uint64_t pol = l2_evict_first_policy();
+    const uint64_t pol = l2_link_policy(ls.keep);
     constexpr int nq = (KIND == 0 || RECON == 18) ? 9 : 6;
     constexpr int ne = (KIND == 0 || RECON == 18) ? 9 : 6;  // stored elements per matrix
     float4 q[nq];
@@ -399,7 +404,7 @@ template <int RECON> struct LinkIO<PREC_F32, RECON> {
                                               const LinkScales &ls, Mat3<float> m[4]) {
     const char *fat = links + (size_t)mu * LL::mu_bytes * S;
     const char *lng = fat + (size_t)LL::fat_bytes * S;
-    const uint64_t pol = l2_evict_first_policy();
+    const uint64_t pol = l2_link_policy(ls.keep);
     float4 q[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) q[k] = ld_stream_f4(fat + ((size_t)k * S + i) * 16, pol);
@@ -452,7 +457,7 @@ template <int RECON> struct LinkIO<PREC_I16, RECON> {
                                               const LinkScales &ls, Mat3<float> m[4]) {
     const char *fat = links + (size_t)mu * LL::mu_bytes * S;
     const char *lng = fat + (size_t)LL::fat_bytes * S;
-    const uint64_t pol = l2_evict_first_policy();
+    const uint64_t pol = l2_link_policy(ls.keep);
     uint32_t w[18];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
