@@ -206,18 +206,23 @@ __device__ __forceinline__ Vec3<float> i16_vector(const uint4 q, float f) {
   return v;
 }
 
-// buf[0] holds direction 0's words on entry (loaded by the caller).
+// buf holds direction 0's words on entry (loaded by the caller before the
+// kernel waited for its predecessor); each later direction's words are
+// loaded at its top.  Measured against keeping the next direction's words
+// in flight: holding one direction needs ~80 registers instead of ~128, the
+// 24 resident warps per SM this allows hide more latency than the prefetch
+// did (20^3 x 64: 23.4 vs 27.0 us; 32^3 x 64: 83.6 vs 94.2 us, 12-real).
 template <int RECON, int NR>
 __device__ __forceinline__ void i16_hops(const DslashArgs &a, const LinkScales &ls,
                                          const SiteCoords &sc, int i, int r0,
                                          const bool (&active)[NR], Vec3<float> (&acc)[NR],
-                                         I16Words<RECON> (&buf)[2]) {
+                                         I16Words<RECON> &buf) {
   const Geom &g = a.g;
   const int S = g.stride;
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
-    if (mu < 3) i16_load_words<RECON>(a.links, S, i, mu + 1, buf[(mu + 1) & 1], ls.keep);
-    const uint32_t *w = buf[mu & 1].w;
+    if (mu > 0) i16_load_words<RECON>(a.links, S, i, mu, buf, ls.keep);
+    const uint32_t *w = buf.w;
     int nb[4];
     float f[4];
     nb[0] = hop<+1>(g, sc, mu, f[0]);
@@ -312,20 +317,34 @@ template <int PREC, int RECON> struct FirstLinks {
 };
 template <int RECON> struct FirstLinks<PREC_I16, RECON> {
   static constexpr bool kUsed = true;
-  I16Words<RECON> buf[2];
+  I16Words<RECON> buf;
   __device__ __forceinline__ void load(const DslashArgs &a, const LinkScales &ls, int i) {
-    i16_load_words<RECON>(a.links, a.g.stride, i, 0, buf[0], ls.keep);
+    i16_load_words<RECON>(a.links, a.g.stride, i, 0, buf, ls.keep);
   }
 };
 
 // Launch bounds per precision: FP64 needs the large register file of the SM
 // (a 512-thread bound squeezes it to 64 registers and spills); FP32 and
 // 16-bit fit 128 registers at up to 512 threads.
-template <int PREC> struct DslashBounds { static constexpr int threads = 512, min_blocks = 1; };
-template <> struct DslashBounds<PREC_F64> { static constexpr int threads = 256, min_blocks = 1; };
+template <int PREC, int NR> struct DslashBounds {
+  static constexpr int threads = (PREC == PREC_F64) ? 256 : 512;
+  static constexpr int min_blocks = 1;
+};
+// One-RHS 16-bit: six 128-thread blocks per SM (at most 85 registers): the
+// kernel is latency-bound and gains more from resident warps than from
+// registers.
+template <> struct DslashBounds<PREC_I16, 1> {
+  static constexpr int threads = 128, min_blocks = 6;
+};
+// Largest block a (precision, RHS tile) kernel may be launched with.
+inline int dslash_max_block(int prec, int nr) {
+  if (prec == PREC_I16 && nr == 1) return DslashBounds<PREC_I16, 1>::threads;
+  return prec == PREC_F64 ? DslashBounds<PREC_F64, 2>::threads : DslashBounds<PREC_F32, 2>::threads;
+}
 
 template <int PREC, int RECON, int NR, int MODE, int OUTP>
-__global__ void __launch_bounds__(DslashBounds<PREC>::threads, DslashBounds<PREC>::min_blocks)
+__global__ void __launch_bounds__(DslashBounds<PREC, NR>::threads,
+                                  DslashBounds<PREC, NR>::min_blocks)
 dslash_kernel(const DslashArgs a) {
   using R = typename AccumType<PREC>::R;
   const Geom &g = a.g;

@@ -11,9 +11,7 @@ int launch_dslash(int prec, int recon, int nr, int mode, int outp, const DslashA
                   int block, cudaStream_t stream) {
   if (a.g.vh <= 0) return 0;
   if (block <= 0 || block % CHUNK != 0 || block > 512) return -1;
-  const int cap = prec == PREC_F64   ? DslashBounds<PREC_F64>::threads
-                  : prec == PREC_F32 ? DslashBounds<PREC_F32>::threads
-                                     : DslashBounds<PREC_I16>::threads;
+  const int cap = dslash_max_block(prec, nr);
   if (block > cap) block = cap;
   switch (prec) {
     case PREC_F64: return launch_dslash_f64(recon, nr, mode, outp, a, block, stream);

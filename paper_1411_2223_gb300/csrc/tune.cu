@@ -132,7 +132,7 @@ DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon
   DslashConfig best_c = def;
   const int reps = 5;
   for (int nr : nrs) {
-    const int max_block = (prec == PREC_F64) ? DslashBounds<PREC_F64>::threads : 512;
+    const int max_block = dslash_max_block(prec, nr);
     for (int block = 128; block <= max_block; block += 128) {
       if (launch_dslash(prec, recon, nr, mode, prec, a, block, st) != 0) continue;
       cudaEventRecord(e0, st);
