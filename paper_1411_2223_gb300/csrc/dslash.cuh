@@ -261,15 +261,20 @@ __device__ __forceinline__ void i16_hops(const DslashArgs &a, const LinkScales &
   }
 }
 
-// ------------------------------------------------------ many right-hand sides
-// With NR >= 8 systems per thread the link stream is no longer the cost (each
-// link is read once for all of them); registers are.  One pair of hop
-// matrices is held at a time and applied to every system, with the hop's
-// sign (eta, backward hop, antiperiodic wrap) folded into the gathered vector.
-template <int RECON, int NR>
-__device__ __forceinline__ void many_rhs_hops(const DslashArgs &a, const LinkScales &ls,
-                                              const SiteCoords &sc, int i, int r0,
-                                              const bool (&active)[NR], Vec3<float> (&acc)[NR]) {
+// ------------------------------------------------------ pair at a time
+// One pair of hop matrices (fat or long) is held at a time and applied to
+// every system of the tile, with the hop's sign (eta, backward hop,
+// antiperiodic wrap) folded into the gathered vector.  Used where registers,
+// not the link stream, limit the kernel: FP32 tiles of 8 or 12 systems (each
+// link read once for all of them) and the one-system FP64 kernels (36
+// doubles of links in registers instead of 72, twice the resident warps for
+// an FP64-bound kernel).
+template <int PREC, int RECON, int NR, int MODE>
+__device__ __forceinline__ void pair_hops(const DslashArgs &a, const LinkScales &ls,
+                                          const SiteCoords &sc, int i, int r0,
+                                          const bool (&active)[NR],
+                                          Vec3<typename AccumType<PREC>::R> (&acc)[NR]) {
+  using R = typename AccumType<PREC>::R;
   const Geom &g = a.g;
   const int S = g.stride;
 #pragma unroll 1
@@ -287,16 +292,18 @@ __device__ __forceinline__ void many_rhs_hops(const DslashArgs &a, const LinkSca
     f[3] *= -eta;
 #pragma unroll
     for (int kind = 0; kind < 2; ++kind) {
-      Mat3<float> m[2];
-      if (kind == 0) LinkIO<PREC_F32, RECON>::template load_pair<0>(a.links, S, i, mu, ls, m);
-      else LinkIO<PREC_F32, RECON>::template load_pair<1>(a.links, S, i, mu, ls, m);
+      Mat3<R> m[2];
+      if (kind == 0) LinkIO<PREC, RECON>::template load_pair<0>(a.links, S, i, mu, ls, m);
+      else LinkIO<PREC, RECON>::template load_pair<1>(a.links, S, i, mu, ls, m);
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         if (!active[r]) continue;
         const char *in = a.in + (size_t)(r0 + r) * a.in_fb;
+        const char *fx = (a.xs != nullptr) ? a.xs + (size_t)(r0 + r) * a.xs_fb : nullptr;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const Vec3<float> v = gather<PREC_F32, float>(in, S, nb[2 * kind + h], f[2 * kind + h]);
+          const Vec3<R> v =
+              gather_in<PREC, MODE, R>(in, fx, a.xs_prec, S, nb[2 * kind + h], f[2 * kind + h]);
           mat_vec_acc(acc[r], m[h], v);
         }
       }
@@ -336,9 +343,15 @@ template <int PREC, int NR> struct DslashBounds {
 template <> struct DslashBounds<PREC_I16, 1> {
   static constexpr int threads = 128, min_blocks = 6;
 };
+// One-RHS FP64: four 128-thread blocks per SM (at most 128 registers) for
+// the pair-at-a-time path.
+template <> struct DslashBounds<PREC_F64, 1> {
+  static constexpr int threads = 128, min_blocks = 4;
+};
 // Largest block a (precision, RHS tile) kernel may be launched with.
 inline int dslash_max_block(int prec, int nr) {
   if (prec == PREC_I16 && nr == 1) return DslashBounds<PREC_I16, 1>::threads;
+  if (prec == PREC_F64 && nr == 1) return DslashBounds<PREC_F64, 1>::threads;
   return prec == PREC_F64 ? DslashBounds<PREC_F64, 2>::threads : DslashBounds<PREC_F32, 2>::threads;
 }
 
@@ -410,8 +423,8 @@ dslash_kernel(const DslashArgs a) {
     const SiteCoords sc = site_coords(g, a.out_parity, i);
     if constexpr (PREC == PREC_I16) {
       i16_hops<RECON, NR>(a, ls, sc, i, r0, active, acc, first.buf);
-    } else if constexpr (PREC == PREC_F32 && NR >= 8) {
-      many_rhs_hops<RECON, NR>(a, ls, sc, i, r0, active, acc);
+    } else if constexpr ((PREC == PREC_F32 && NR >= 8) || (PREC == PREC_F64 && NR == 1)) {
+      pair_hops<PREC, RECON, NR, MODE>(a, ls, sc, i, r0, active, acc);
     } else {
 #pragma unroll 1
       for (int mu = 0; mu < 4; ++mu) {

@@ -340,6 +340,24 @@ template <int PREC, int RECON> struct LinkIO;
 
 template <int RECON> struct LinkIO<PREC_F64, RECON> {
   using LL = LinkLayout<PREC_F64, RECON>;
+  // One pair of direction mu: the fat pair for KIND 0, the long pair for 1.
+  template <int KIND>
+  static __device__ __forceinline__ void load_pair(const char *links, int S, int i, int mu,
+                                                   const LinkScales &ls, Mat3<double> m[2]) {
+    const char *base = links + (size_t)mu * LL::mu_bytes * S;
+    if (KIND == 1) base += (size_t)LL::fat_bytes * S;
+    const uint64_t pol = l2_link_policy(ls.keep);
+    constexpr int ne = (KIND == 0 || RECON == 18) ? 9 : 6;  // stored elements per matrix
+#pragma unroll
+    for (int k = 0; k < ne; ++k) {
+      m[0].e[k] = ld_stream_d2(base + ((size_t)k * S + i) * 16, pol);
+      m[1].e[k] = ld_stream_d2(base + ((size_t)(ne + k) * S + i) * 16, pol);
+    }
+    if constexpr (ne == 6) {
+      reconstruct_row2(m[0], ls.recon_d);
+      reconstruct_row2(m[1], ls.recon_d);
+    }
+  }
   static __device__ __forceinline__ void load(const char *links, int S, int i, int mu,
                                               const LinkScales &ls, Mat3<double> m[4]) {
     const char *fat = links + (size_t)mu * LL::mu_bytes * S;
