@@ -1,9 +1,13 @@
-"""FP64 CPU oracle for the asqtad even-odd CG -- TEST INFRASTRUCTURE.
+"""FP64 CPU oracle for the asqtad even-odd CG and the NPR four-fermion
+operator (Eq. 1) -- TEST INFRASTRUCTURE.
 
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` import this package.  The GPU library neither imports nor links
 it, and the two share no code: the oracle is plain C (``oracle.c``) written
 site by site from the operator definitions, driven through ctypes.
+
+The NPR part builds the hypercube spin-taste matrices here, from explicit
+Dirac matrices and traces, and evaluates Eq. 1 term by term in C.
 
 Vectors here are numpy complex128 arrays.  Full-lattice vectors have shape
 ``(V, 3)`` indexed by ``site_lex``; parity-half vectors have shape
@@ -70,6 +74,8 @@ def _load():
             lib.oracle_quantize_links_i16.argtypes = [Lg, P, D, P]
             lib.oracle_fat_long.argtypes = [P, P, D, D, D, P, P]
             lib.oracle_asqtad_links.argtypes = [P, P, P, P, P]
+            lib.oracle_npr_avg_link.argtypes = [P, P, P, I, I, P]
+            lib.oracle_npr.argtypes = [P, P, P, P, P, P, I, P, P, Lg, P, P]
             _lib = lib
     return _lib
 
@@ -303,3 +309,91 @@ def quantize_links_i16(values, scale):
     q = np.zeros(v.shape[0], dtype=np.int16)
     lib.oracle_quantize_links_i16(v.shape[0], _ptr(v), float(scale), _ptr(q))
     return q.reshape(np.shape(values))
+
+
+# ------------------------------------------- NPR four-fermion operator (Eq. 1)
+
+def gammas():
+    """Euclidean Dirac matrices gamma_1..gamma_4 (Hermitian, {g_mu, g_nu} =
+    2 delta), chiral basis: g_k = [[0, -i s_k], [i s_k, 0]], g_4 = [[0, 1],
+    [1, 0]].  Shape (4, 4, 4); index mu = 0..3 is gamma_{mu+1}."""
+    s = [np.array([[0, 1], [1, 0]], dtype=np.complex128),
+         np.array([[0, -1j], [1j, 0]], dtype=np.complex128),
+         np.array([[1, 0], [0, -1]], dtype=np.complex128)]
+    z = np.zeros((2, 2), dtype=np.complex128)
+    one = np.eye(2, dtype=np.complex128)
+    g = [np.block([[z, -1j * sk], [1j * sk, z]]) for sk in s]
+    g.append(np.block([[z, one], [one, z]]))
+    return np.stack(g)
+
+
+def gamma_of(x, g=None):
+    """gamma_X = g_1^{X_0} g_2^{X_1} g_3^{X_2} g_4^{X_3} for a hypercube vector
+    X given as a 4-bit mask (bit mu = X_mu)."""
+    g = gammas() if g is None else g
+    m = np.eye(4, dtype=np.complex128)
+    for mu in range(4):
+        if (x >> mu) & 1:
+            m = m @ g[mu]
+    return m
+
+
+def spin_taste(s, f, g=None):
+    """The hypercube spin-taste matrix of Eq. 1, (gamma_S x xi_F)_{AB} =
+    Tr(gamma_A^dag gamma_S gamma_B gamma_F^dag) / 4, A, B = 0..15 (16 x 16
+    complex).  S and F are 4-bit masks."""
+    g = gammas() if g is None else g
+    gs, gf = gamma_of(s, g), gamma_of(f, g)
+    m = np.zeros((16, 16), dtype=np.complex128)
+    for a in range(16):
+        ga = gamma_of(a, g)
+        for b in range(16):
+            m[a, b] = np.trace(ga.conj().T @ gs @ gamma_of(b, g) @ gf.conj().T) / 4
+    return m
+
+
+def hypercube_count(dims):
+    return volume(dims) // 16
+
+
+def hypercube_index(dims, z):
+    """Index of hypercube z = (z_x, z_y, z_z, z_t), 0 <= z_mu < L_mu / 2."""
+    h = [int(d) // 2 for d in dims]
+    return int(z[0] + h[0] * (z[1] + h[1] * (z[2] + h[2] * z[3])))
+
+
+def npr_avg_link(dims, links, z, a, d):
+    """U_AD(z): the mean of the links' products over all shortest paths from
+    corner A to corner D of hypercube z (Eq. 1).  3 x 3 complex."""
+    lib = _load()
+    u = _c128(links)
+    out = np.zeros((3, 3), dtype=np.complex128)
+    zz = np.ascontiguousarray(z, dtype=np.int32)
+    lib.oracle_npr_avg_link(_ptr(_dims(dims)), _ptr(u), _ptr(zz), int(a), int(d), _ptr(out))
+    return out
+
+
+def npr_four_fermion(dims, links, props, ops, hypercubes=None, g=None):
+    """The one-colour four-fermion operator of Eq. 1 on every hypercube (or
+    the listed hypercube indices), for each operator (S1, F1, S2, F2) of ops.
+
+    props: four propagators (V, 3, 3) complex, [site][colour][source colour];
+    flavours 1 and 3 enter as chibar (conjugated columns), 2 and 4 as chi.
+    Returns (nz, nops, 3, 3, 3, 3) complex, axes [z][op][a1][a2][a3][a4]."""
+    lib = _load()
+    u = _c128(links)
+    gs = [_c128(p) for p in props]
+    assert len(gs) == 4 and all(p.shape == (volume(dims), 3, 3) for p in gs)
+    nops = len(ops)
+    m1 = np.ascontiguousarray(np.stack([spin_taste(o[0], o[1], g) for o in ops]))
+    m2 = np.ascontiguousarray(np.stack([spin_taste(o[2], o[3], g) for o in ops]))
+    if hypercubes is None:
+        nz, zl = hypercube_count(dims), None
+    else:
+        zl = np.ascontiguousarray(hypercubes, dtype=np.int64)
+        nz = len(zl)
+    out = np.zeros((nz, nops, 3, 3, 3, 3), dtype=np.complex128)
+    lib.oracle_npr(_ptr(_dims(dims)), _ptr(u), _ptr(gs[0]), _ptr(gs[1]), _ptr(gs[2]),
+                   _ptr(gs[3]), nops, _ptr(m1), _ptr(m2), nz,
+                   None if zl is None else _ptr(zl), _ptr(out))
+    return out

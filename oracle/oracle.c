@@ -1,5 +1,7 @@
 /*
- * Plain FP64 CPU oracle for the asqtad even-odd CG.  TEST INFRASTRUCTURE ONLY:
+ * Plain FP64 CPU oracle for the asqtad even-odd CG, and for the NPR
+ * four-fermion operator of Sec. 3, Eq. 1 (at the end of this file).
+ * TEST INFRASTRUCTURE ONLY:
  * the tests, the smoke check and the benchmark's CPU-baseline leg call it; the
  * GPU library never does, and the two share no code.
  *
@@ -595,4 +597,130 @@ void oracle_asqtad_links(const int L[4], const double *u, const double coef[6], 
         }
     }
     free(umu); free(acc); free(p3); free(p5); free(p7); free(lp);
+}
+
+/*
+ * ---- NPR one-colour four-fermion operator (Sec. 3, Eq. 1) ----
+ *
+ * Hypercube z (0 <= z_mu < L_mu / 2) has the 16 corner sites z_A = 2z + A,
+ * A in {0,1}^4, indexed A = A_x + 2 A_y + 4 A_z + 8 A_t.
+ *
+ * Averaged link U_AD(z): the mean over the n! shortest paths inside the
+ * hypercube from z_A to z_D (n = number of directions in which A and D
+ * differ), each path the ordered product of its links; a step +mu from y
+ * multiplies by U_mu(y), a step -mu by U_mu(y - mu)^dag.  U_AA = 1.
+ *
+ * Quark fields are propagator columns: chi^f_c(x) = G^f(x)[c][a] and
+ * chibar^f_c(x) = conj(G^f(x)[c][a]), with a the source colour.  For one
+ * operator with hypercube spin-taste matrices M1, M2 (16 x 16, input):
+ *   O[a1][a2][a3][a4](z) = sum_{A,B,C,D} sum_{c1..c4}
+ *       chibar^1_{c1}(z_A) M1[A][B] chi^2_{c2}(z_B)
+ *     * chibar^3_{c3}(z_C) M2[C][D] chi^4_{c4}(z_D)
+ *     * U_AD[c1][c4] * U_CB[c3][c2],
+ * each chibar/chi taking the source colour a_f of its flavour f.
+ *
+ * Arrays: links as above; propagators [site_lex][c][a] complex; m1, m2
+ * [op][A][B] complex; out [k][op][a1][a2][a3][a4] complex for the k-th
+ * hypercube of zlist (hypercube index z_x + Hx (z_y + Hy (z_z + Hz z_t)),
+ * H = L / 2), or of all hypercubes in order when zlist is NULL.
+ */
+static long corner_site(const int L[4], const int z[4], int a)
+{
+    int c[4];
+    for (int mu = 0; mu < 4; mu++) c[mu] = 2 * z[mu] + ((a >> mu) & 1);
+    return oracle_lex(L, c);
+}
+
+/* Adds the products of all shortest paths from corner x to corner d, each
+ * pre-multiplied by prod (the path so far), to acc; counts them in *npaths. */
+static void path_sum(const int L[4], const double *u, const int z[4], int x, int d,
+                     const cplx *prod, cplx *acc, int *npaths)
+{
+    if (x == d) {
+        for (int e = 0; e < 9; e++) acc[e] += prod[e];
+        (*npaths)++;
+        return;
+    }
+    for (int mu = 0; mu < 4; mu++) {
+        if (!(((x ^ d) >> mu) & 1)) continue;
+        int y = x ^ (1 << mu);
+        cplx next[9];
+        if (((x >> mu) & 1) == 0)     /* forward step: U_mu(z_x) */
+            mat_mul(next, prod, link_at(u, corner_site(L, z, x), mu), 0, 0);
+        else                          /* backward step: U_mu(z_y)^dag */
+            mat_mul(next, prod, link_at(u, corner_site(L, z, y), mu), 0, 1);
+        path_sum(L, u, z, y, d, next, acc, npaths);
+    }
+}
+
+void oracle_npr_avg_link(const int L[4], const double *u, const int z[4], int a, int d,
+                         double *out)
+{
+    cplx one[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    cplx acc[9] = {0};
+    int npaths = 0;
+    path_sum(L, u, z, a, d, one, acc, &npaths);
+    cplx *o = (cplx *)out;
+    for (int e = 0; e < 9; e++) o[e] = acc[e] / npaths;
+}
+
+void oracle_npr(const int L[4], const double *u, const double *g1, const double *g2,
+                const double *g3, const double *g4, int nops, const double *m1,
+                const double *m2, long nz, const long *zlist, double *out)
+{
+    const int H[4] = {L[0] / 2, L[1] / 2, L[2] / 2, L[3] / 2};
+    #pragma omp parallel for schedule(dynamic)
+    for (long k = 0; k < nz; k++) {
+        long zi = zlist ? zlist[k] : k;
+        int z[4];
+        for (int mu = 0; mu < 4; mu++) {
+            z[mu] = (int)(zi % H[mu]);
+            zi /= H[mu];
+        }
+        cplx (*U)[16][9] = malloc(sizeof(cplx) * 16 * 16 * 9);
+        const cplx *G[4][16];
+        for (int a = 0; a < 16; a++) {
+            long s = corner_site(L, z, a);
+            G[0][a] = (const cplx *)(g1 + s * 18);
+            G[1][a] = (const cplx *)(g2 + s * 18);
+            G[2][a] = (const cplx *)(g3 + s * 18);
+            G[3][a] = (const cplx *)(g4 + s * 18);
+            for (int d = 0; d < 16; d++) oracle_npr_avg_link(L, u, z, a, d, (double *)U[a][d]);
+        }
+        for (int op = 0; op < nops; op++) {
+            const cplx *M1 = (const cplx *)m1 + (long)op * 256;
+            const cplx *M2 = (const cplx *)m2 + (long)op * 256;
+            cplx *o = (cplx *)out + (k * nops + op) * 81;
+            for (int e = 0; e < 81; e++) o[e] = 0;
+            for (int A = 0; A < 16; A++)
+            for (int B = 0; B < 16; B++) {
+                cplx mab = M1[A * 16 + B];
+                if (mab == 0) continue;
+                for (int C = 0; C < 16; C++)
+                for (int D = 0; D < 16; D++) {
+                    cplx mcd = M2[C * 16 + D];
+                    if (mcd == 0) continue;
+                    for (int a1 = 0; a1 < 3; a1++)
+                    for (int a2 = 0; a2 < 3; a2++)
+                    for (int a3 = 0; a3 < 3; a3++)
+                    for (int a4 = 0; a4 < 3; a4++) {
+                        /* chibar^1(z_A) U_AD chi^4(z_D) */
+                        cplx s14 = 0;
+                        for (int c1 = 0; c1 < 3; c1++)
+                            for (int c4 = 0; c4 < 3; c4++)
+                                s14 += conj(G[0][A][3 * c1 + a1]) * U[A][D][3 * c1 + c4] *
+                                       G[3][D][3 * c4 + a4];
+                        /* chibar^3(z_C) U_CB chi^2(z_B) */
+                        cplx s32 = 0;
+                        for (int c3 = 0; c3 < 3; c3++)
+                            for (int c2 = 0; c2 < 3; c2++)
+                                s32 += conj(G[2][C][3 * c3 + a3]) * U[C][B][3 * c3 + c2] *
+                                       G[1][B][3 * c2 + a2];
+                        o[27 * a1 + 9 * a2 + 3 * a3 + a4] += mab * mcd * s14 * s32;
+                    }
+                }
+            }
+        }
+        free(U);
+    }
 }

@@ -22,3 +22,4 @@ from .gauge import (  # noqa: F401
     gauge_field, gauge_transform_links, shift_field, lattice_volume,
 )
 from .fields import gaussian_source, gaussian_sources, parity_sites  # noqa: F401
+from . import npr  # noqa: F401
