@@ -40,7 +40,7 @@ CG_FLOPS_PER_SITE_ITER = 2364
 PAPER_CONTEXT_GFLOPS = 46.48   # mixed-precision CG, GTX Titan Black (Table 2)
 # DRAM traffic of one FP32 18-real Dslash launch at 20^3 x 64 from an ncu
 # capture of the kernel source with this fingerprint (None: not captured).
-NCU_TRAFFIC = {'fingerprint': '2aba04019599587a', 'bytes_per_launch': 306.2e6}
+NCU_TRAFFIC = {'fingerprint': '294aa6911b14d63a', 'bytes_per_launch': 306.2e6}
 
 
 def parse_args():
@@ -61,7 +61,10 @@ def parse_args():
                    help='profiling aid: only time the Dslash in these formats '
                         '(comma list of prec_recon, e.g. f32_18), no solves')
     p.add_argument('--dims', default=None, metavar='LX,LY,LZ,LT',
-                   help='lattice of the --dslash-only run (default 20,20,20,64)')
+                   help='lattice of the --dslash-only / --npr-only run (default 20,20,20,64)')
+    p.add_argument('--npr-only', action='store_true',
+                   help='profiling aid: only run the NPR four-fermion workload')
+    p.add_argument('--npr-reps', type=int, default=3)
     return p.parse_args()
 
 
@@ -397,6 +400,71 @@ def full_lattice_workload(ctx, sq, stream, fat, lng):
                                     'peak_kind': 'measured FP64 DGEMM (torch.matmul 4096^3)'}}}
 
 
+# Flops of one hypercube of the NPR operator (Eq. 1), counting 8 per complex
+# multiply-add of the factored evaluation: averaged links 224 SU(3) products
+# (U_AD for A < D at distance >= 2, the recursion over the first step), the
+# sandwiches P = G1^dag U G4 and Q = G3^dag U G2 (2 x 256 pairs x 2
+# products), and per operator 256 corner pairs x 81 outputs.
+def npr_flops_per_hypercube(nops):
+    return 8 * (224 * 27 + 2 * 256 * 2 * 27 + 256 * 81 * nops)
+
+
+NPR_PAPER_GFLOPS = 113.36   # NPR four-fermion part, GTX Titan Black, 1 GPU (Table 3)
+
+
+def npr_workload(ctx, stream, dims=DIMS, reps=3):
+    """The NPR one-colour four-fermion operator (Eq. 1) over the 20^3 x 64
+    lattice: thin links (eps 0.25, seed 0), four Gaussian propagators (seed 1),
+    the 8 B_K-basis operators; sums over hypercubes only (no per-hypercube
+    output).  FP64 throughput against the measured DGEMM rate.  Returns the
+    result and the host inputs (for the CPU baseline)."""
+    import numpy as np
+    import torch
+    import synth
+    from synth import npr as snpr
+    vol = int(np.prod(dims))
+    nhc = vol // 16
+    links = synth.thin_links(dims, EPS, GAUGE_SEED)
+    props = snpr.propagators(dims, 1)
+    ops = snpr.bk_ops()
+    u = torch.from_numpy(links).cuda()
+    ps = [torch.from_numpy(p).cuda() for p in props]
+    out = torch.empty((len(ops), 3, 3, 3, 3), dtype=torch.complex128, device='cuda')
+    with torch.cuda.stream(stream):
+        ctx.npr_four_fermion(dims, u, ps, ops, out, stream=stream)
+        ms, _ = timed(lambda: ctx.npr_four_fermion(dims, u, ps, ops, out, stream=stream),
+                      stream, reps)
+    flops = npr_flops_per_hypercube(len(ops)) * nhc
+    tflops = flops / (ms * 1e-3) / 1e12
+    peak = fp64_peak_tflops()
+    res = {'workload': '%s NPR one-colour four-fermion operator (Eq. 1), FP64: thin links '
+                       '(eps 0.25, seed 0), 4 Gaussian propagators (seed 1), 8 B_K-basis '
+                       'operators, summed over %d hypercubes' % ('x'.join(map(str, dims)), nhc),
+           'ms': round(ms, 3), 'gflops_fp64': round(tflops * 1e3, 1),
+           'flops_per_hypercube': npr_flops_per_hypercube(len(ops)),
+           'roofline': {'bound': 'alu', 'achieved': round(tflops, 4), 'peak': round(peak, 4),
+                        'unit': 'TFLOP/s', 'frac': round(tflops / peak, 4),
+                        'peak_kind': 'measured FP64 DGEMM (torch.matmul 4096^3)'},
+           'paper_context': {'gflops_titan_black_1gpu': NPR_PAPER_GFLOPS,
+                             'note': 'Table 3; different hardware and flop convention'}}
+    return res, (dims, links, props, ops)
+
+
+def npr_cpu_baseline(inputs, n_hc=512):
+    """The oracle's NPR operator on the host cores for the first n_hc
+    hypercubes of the workload, scaled to the whole lattice."""
+    import oracle
+    dims, links, props, ops = inputs
+    nhc = (dims[0] * dims[1] * dims[2] * dims[3]) // 16
+    t0 = time.perf_counter()
+    oracle.npr_four_fermion(dims, links, props, ops, hypercubes=list(range(n_hc)))
+    dt = time.perf_counter() - t0
+    return {'value': round(dt * 1e3 * nhc / n_hc, 1), 'unit': 'ms', 'cores': os.cpu_count(),
+            'kind': 'oracle',
+            'sample': '%d of %d hypercubes x %d operators (%.1f s), scaled to the lattice'
+                      % (n_hc, nhc, len(ops), dt)}
+
+
 def batched_workload(ctx, sq, stream):
     """24^3 x 64: 12 right-hand sides in one batched solve against 12 single
     solves, and 8 masses in one multi-shift solve against 8 single solves."""
@@ -510,6 +578,13 @@ def main():
     if args.dslash_only and args.dims:
         dims = tuple(int(v) for v in args.dims.split(','))
     vh = int(np.prod(dims)) // 2
+    if args.npr_only:
+        ndims = tuple(int(v) for v in args.dims.split(',')) if args.dims else DIMS
+        ctx = sq.Context(local)
+        res, _ = npr_workload(ctx, torch.cuda.Stream(), ndims, args.npr_reps)
+        print(json.dumps({'npr': res}))
+        ctx.close()
+        return 0
 
     fat, lng = synth.gauge_field(dims, EPS, GAUGE_SEED)
     b_host = synth.gaussian_source(vh, SRC_SEED)
@@ -624,9 +699,10 @@ def main():
                 if peak_kind == 'measured' else 'fallback'}
 
     serve = serve_bench(ctx, args.serve_requests, sq) if args.serve_requests > 0 else None
-    extra_i16 = extra_batch = extra_full = None
+    extra_i16 = extra_batch = extra_full = extra_npr = None
     if not args.no_extra:
         ctx.gauge_free(gid)
+        extra_npr, npr_inputs = npr_workload(ctx, stream)
         extra_full = full_lattice_workload(ctx, sq, stream, fat, lng)
         extra_i16 = i16_workload(ctx, sq, stream, args.dslash_iters)
         extra_batch = batched_workload(ctx, sq, stream)
@@ -634,6 +710,8 @@ def main():
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(fat, lng, b_host, args.cpu_sample_s)
+        if extra_npr is not None:
+            cb['npr_20x64'] = npr_cpu_baseline(npr_inputs)
 
     if rank == 0:
         gflops = CG_FLOPS_PER_SITE_ITER * vh * iters / (ms * 1e-3) / 1e9
@@ -656,6 +734,7 @@ def main():
             'i16_32x64': extra_i16,
             'batched_24x64': extra_batch,
             'whole_lattice_20x64': extra_full,
+            'npr_20x64': extra_npr,
             'roofline': roofline,
             'e2e': {'value': round(ms_e2e, 3), 'unit': 'ms', 'h2d_bytes_per_step': h2d,
                     'd2h_bytes_per_step': d2h},

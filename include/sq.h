@@ -180,6 +180,46 @@ int gauge_fatten_asqtad(sq_ctx *ctx, const int dims[4], const double *thin_dev,
 int gauge_load_thin(sq_ctx *ctx, const int dims[4], const double *thin, double c1, double c3,
                     double staple_weight, unsigned flags, int *gauge_id);
 
+/* ---- NPR four-fermion operator (Sec. 2, Eq. 1, Fig. 2, Table 3) ---------- */
+
+#define SQ_NPR_MAX_OPS 16
+
+/* The hypercube spin-taste matrix of Eq. 1,
+ *   (gamma_S x xi_F)_{AB} = Tr(gamma_A^dag gamma_S gamma_B gamma_F^dag) / 4,
+ * gamma_X = gamma_1^{X_0} gamma_2^{X_1} gamma_3^{X_2} gamma_4^{X_3} (Euclidean),
+ * in the form the GPU uses: row A has one nonzero entry, sign[A] (+1 or -1)
+ * at column partner[A] = A ^ S ^ F.  S, F, A: 4-bit masks, bit mu for
+ * direction mu = x, y, z, t.  Host only (no device work); SQ_ERR_ARG for a
+ * mask outside 0..15 or a null array. */
+int sq_spin_taste(int s, int f, int partner[16], int sign[16]);
+
+/* The one-colour four-fermion operator of the paper's NPR code, Eq. 1, in
+ * FP64 on the device, for nops operators (S1, F1, S2, F2) (4-bit masks, host
+ * array ops[nops][4], 0 <= nops <= SQ_NPR_MAX_OPS):
+ *   O[a1][a2][a3][a4](z) = sum_{A,B,C,D} sum_{c1..c4}
+ *       conj(G1(z_A)[c1][a1]) (gamma_S1 x xi_F1)_{AB} G2(z_B)[c2][a2]
+ *     * conj(G3(z_C)[c3][a3]) (gamma_S2 x xi_F2)_{CD} G4(z_D)[c4][a4]
+ *     * U_AD(z)[c1][c4] U_CB(z)[c3][c2]
+ * over the hypercubes z (0 <= z_mu < L_mu / 2) with corner sites
+ * z_A = 2z + A.  U_AD(z) is the mean of the link products over the shortest
+ * paths from z_A to z_D inside the hypercube (a step +mu from y is U_mu(y), a
+ * step -mu is U_mu(y-mu)^dag).  The quark fields are the source-colour
+ * columns a of the propagators G^f, the antiquark fields (flavours 1, 3)
+ * their complex conjugates.
+ *   links_dev   device, [site_lex][mu][3][3] complex128 (any links: thin or
+ *               smeared);
+ *   props_dev   four device arrays, [site_lex][colour][source colour]
+ *               complex128;
+ *   out_dev     device, [op][a1][a2][a3][a4] complex128: the sum over z;
+ *   out_hc_dev  NULL, or device [z][op][a1][a2][a3][a4] complex128 with
+ *               z = z_x + Hx (z_y + Hy (z_z + Hz z_t)), H = L / 2.
+ * Device arrays 16-byte aligned; all extents even.  Asynchronous on `stream`
+ * (a stream-ordered scratch of 16 * 81 * nops bytes per CTA is taken and
+ * returned on it).  The sum over z is deterministic. */
+int npr_four_fermion(sq_ctx *ctx, const int dims[4], const double *links_dev,
+                     const double *const props_dev[4], int nops, const int *ops,
+                     double *out_dev, double *out_hc_dev, void *stream);
+
 /* Bytes of one packed parity-half vector of `prec` for this gauge field's
  * lattice, and the plane stride in sites. */
 int sq_spinor_bytes(sq_ctx *ctx, int gauge_id, int prec, size_t *bytes, int *stride);

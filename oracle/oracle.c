@@ -1,6 +1,6 @@
 /*
  * Plain FP64 CPU oracle for the asqtad even-odd CG, and for the NPR
- * four-fermion operator of Sec. 3, Eq. 1 (at the end of this file).
+ * four-fermion operator of Sec. 2, Eq. 1 (at the end of this file).
  * TEST INFRASTRUCTURE ONLY:
  * the tests, the smoke check and the benchmark's CPU-baseline leg call it; the
  * GPU library never does, and the two share no code.
@@ -600,7 +600,7 @@ void oracle_asqtad_links(const int L[4], const double *u, const double coef[6], 
 }
 
 /*
- * ---- NPR one-colour four-fermion operator (Sec. 3, Eq. 1) ----
+ * ---- NPR one-colour four-fermion operator (Sec. 2, Eq. 1) ----
  *
  * Hypercube z (0 <= z_mu < L_mu / 2) has the 16 corner sites z_A = 2z + A,
  * A in {0,1}^4, indexed A = A_x + 2 A_y + 4 A_z + 8 A_t.

@@ -255,16 +255,6 @@ __global__ void __launch_bounds__(128) asqtad_kernel(FatGeom g, const double2 *u
   for (int e = 0; e < 9; ++e) l[e] = make_double2(k.naik * n.e[e].x, k.naik * n.e[e].y);
 }
 
-int check_dims(const int dims[4], long *vol) {
-  long v = 1;
-  for (int mu = 0; mu < 4; ++mu) {
-    if (dims[mu] < 2 || (dims[mu] & 1)) return SQ_ERR_ARG;
-    v *= dims[mu];
-    if (v > (1L << 30)) return SQ_ERR_ARG;
-  }
-  *vol = v;
-  return SQ_OK;
-}
 
 int launch_fatten(const int dims[4], long vol, const double *thin, double c1, double c3, double w,
                   double *fat, double *lng, cudaStream_t st) {
@@ -295,6 +285,18 @@ FatGeom make_fat_geom(const int dims[4], long vol) {
 }
 
 }  // namespace
+
+int check_lattice_dims(const int dims[4], long *vol) {
+  long v = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    if (dims[mu] < 2 || (dims[mu] & 1)) return SQ_ERR_ARG;
+    v *= dims[mu];
+    if (v > (1L << 30)) return SQ_ERR_ARG;
+  }
+  *vol = v;
+  return SQ_OK;
+}
+
 }  // namespace sq
 
 using namespace sq;
@@ -306,7 +308,7 @@ extern "C" int gauge_fatten_asqtad(sq_ctx *ctx, const int dims[4], const double 
   for (int k = 0; k < 6; ++k)
     if (!std::isfinite(coeffs[k])) return SQ_ERR_ARG;
   long vol;
-  int rc = check_dims(dims, &vol);
+  int rc = check_lattice_dims(dims, &vol);
   if (rc) return rc;
   cudaSetDevice(ctx->device);
   cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
@@ -328,7 +330,7 @@ extern "C" int gauge_fatten(sq_ctx *ctx, const int dims[4], const double *thin_d
       1.0 + 6.0 * staple_weight == 0.0)
     return SQ_ERR_ARG;
   long vol;
-  int rc = check_dims(dims, &vol);
+  int rc = check_lattice_dims(dims, &vol);
   if (rc) return rc;
   cudaSetDevice(ctx->device);
   cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
@@ -341,7 +343,7 @@ extern "C" int gauge_load_thin(sq_ctx *ctx, const int dims[4], const double *thi
                                double c3, double staple_weight, unsigned flags, int *gauge_id) {
   if (!ctx || !dims || !thin || !gauge_id) return SQ_ERR_ARG;
   long vol;
-  int rc = check_dims(dims, &vol);
+  int rc = check_lattice_dims(dims, &vol);
   if (rc) return rc;
   const size_t nbytes = (size_t)vol * 4 * 9 * 16;
   cudaSetDevice(ctx->device);

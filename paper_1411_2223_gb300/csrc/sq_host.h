@@ -30,6 +30,10 @@ struct Tuner;
 
 void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 
+// Lattice extents all even and >= 2, volume <= 2^30: SQ_OK and *vol, else
+// SQ_ERR_ARG.
+int check_lattice_dims(const int dims[4], long *vol);
+
 struct GaugeField {
   int id = 0;
   Geom g{};

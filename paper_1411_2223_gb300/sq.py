@@ -104,6 +104,8 @@ SIGNATURES = {
     'serve_cancel': (_I, [_P, _U64]),
     'serve_stats': (_I, [_P, ctypes.POINTER(ServeStats), _I]),
     'serve_configure': (_I, [_P, _I, _I]),
+    'sq_spin_taste': (_I, [_I, _I, _P, _P]),
+    'npr_four_fermion': (_I, [_P, _P, _P, _P, _I, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -410,6 +412,30 @@ class Context:
         _check(self._lib.dirac_apply(self.handle, gauge_id, float(mass), _ptr(in_dev),
                                      _ptr(out_dev), _stream(stream)), 'dirac_apply')
 
+    # ------------------------------------------------- NPR operator (Eq. 1)
+    NPR_MAX_OPS = 16
+
+    def npr_four_fermion(self, dims, links_dev, props_dev, ops, out_dev, out_hc_dev=None,
+                         stream=None):
+        """The one-colour four-fermion operator of Eq. 1 on the device, FP64.
+
+        links_dev: (V, 4, 3, 3) complex128; props_dev: four (V, 3, 3)
+        complex128 propagators [site][colour][source colour]; ops: list of
+        (S1, F1, S2, F2) 4-bit masks; out_dev: (nops, 3, 3, 3, 3) complex128,
+        the sum over hypercubes; out_hc_dev: None or (V/16, nops, 3, 3, 3, 3)
+        complex128 per hypercube.  Asynchronous on `stream`."""
+        d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+        if len(props_dev) != 4:
+            raise ValueError('four propagators')
+        pp = (ctypes.c_void_p * 4)(*[_ptr(p) for p in props_dev])
+        flat = [int(v) for op in ops for v in op]
+        if len(flat) != 4 * len(ops):
+            raise ValueError('ops are (S1, F1, S2, F2) tuples')
+        oa = (ctypes.c_int * max(1, len(flat)))(*flat)
+        _check(self._lib.npr_four_fermion(self.handle, d, _ptr(links_dev), pp, len(ops), oa,
+                                          _ptr(out_dev), _ptr(out_hc_dev), _stream(stream)),
+               'npr_four_fermion')
+
     # --------------------------------------------------------------- serving
     def serve_configure(self, slots_per_batch=8, block_iters=8):
         _check(self._lib.serve_configure(self.handle, int(slots_per_batch), int(block_iters)),
@@ -440,6 +466,17 @@ class Context:
         return st.as_dict()
 
 
+def spin_taste(s, f):
+    """The hypercube spin-taste matrix (gamma_S x xi_F) as the library uses
+    it: (partner, sign), row A having its one entry sign[A] at partner[A].
+    Host only."""
+    lib = load_library()
+    partner = (ctypes.c_int * 16)()
+    sign = (ctypes.c_int * 16)()
+    _check(lib.sq_spin_taste(int(s), int(f), partner, sign), 'sq_spin_taste')
+    return list(partner), list(sign)
+
+
 def _forward(name):
     def f(ctx, *args, **kw):
         return getattr(ctx, name)(*args, **kw)
@@ -450,6 +487,6 @@ def _forward(name):
 
 for _n in ('gauge_load', 'gauge_free', 'gauge_fatten', 'gauge_load_thin', 'gauge_fatten_asqtad', 'dslash_apply', 'mdagm_apply', 'cg_solve',
            'cg_solve_multi', 'cg_solve_multishift', 'cg_solve_full', 'dirac_apply',
-           'serve_submit', 'serve_poll',
+           'npr_four_fermion', 'serve_submit', 'serve_poll',
            'serve_cancel', 'serve_stats', 'serve_configure'):
     globals()[_n] = _forward(_n)

@@ -55,3 +55,23 @@ def test_host_only_calls_without_gpu(lib):
     assert l.gauge_load(None, None, None, None, 0, None) == sq.ERR_ARG
     assert l.sq_destroy(None) == sq.ERR_ARG
     assert l.sq_kernel_launches(None) == 0
+
+
+def test_spin_taste_host_rule_matches_oracle_traces(lib):
+    """The library's sign rule for (gamma_S x xi_F) (host code, used to build
+    the GPU's operator tables) against the oracle's explicit Dirac-matrix
+    traces, for all 256 (S, F)."""
+    import numpy as np
+
+    import oracle
+    from paper_1411_2223_gb300 import sq as sqmod
+    for s in range(16):
+        for f in range(16):
+            partner, sign = sqmod.spin_taste(s, f)
+            m = np.zeros((16, 16))
+            m[np.arange(16), partner] = sign
+            ref = oracle.spin_taste(s, f)
+            assert np.abs(ref.imag).max() < 1e-15
+            assert np.array_equal(m, np.rint(ref.real)), (s, f)
+    with pytest.raises(sqmod.SqError):
+        sqmod.spin_taste(16, 0)
