@@ -13,8 +13,8 @@
 // to z_D.  The propagators G^f are [site][colour][source colour]; flavours 1
 // and 3 enter conjugated, as the antiquark fields of Eq. 1.
 //
-// One CTA works on one hypercube at a time (persistent grid, two CTAs per
-// SM), in shared memory:
+// One CTA works on one hypercube at a time (persistent grid, one CTA of 512
+// threads per SM), in shared memory:
 //   1. the 16 corners' propagators and the 32 links inside the hypercube
 //      arrive by cp.async, prefetched while the previous hypercube's
 //      contraction runs;
@@ -25,10 +25,11 @@
 //   3. P[A][D] = G1(A)^dag U_AD G4(D) and Q[C][B] = G3(C)^dag U_CB G2(B) for
 //      all 256 corner pairs, shared by every operator;
 //   4. per operator and output, the 256-term sum over (A, C) of
-//      +-P[A][C ^ t2][a1][a4] Q[C][A ^ t1][a3][a2], t = S ^ F.
+//      +-P[A][C ^ t2][a1][a4] Q[C][A ^ t1][a3][a2], t = S ^ F, with three real
+//      multiply-adds per complex term (contract below).
 // All of it is FP64 arithmetic (about 1.6 MFLOP per hypercube for 8
-// operators against 14 KB of input), so the kernel is bound by the FP64
-// units, not by HBM.  Per-hypercube results are written when asked for; the
+// operators, counting 8 per complex multiply-add, against 14 KB of input), so
+// the kernel is bound by the FP64 units, not by HBM.  Per-hypercube results are written when asked for; the
 // sums over hypercubes go through per-CTA partials and a fixed-order second
 // pass, so they do not depend on scheduling.
 #include <cmath>
@@ -61,12 +62,13 @@ int spin_taste_sign(int s, int f, int a) {
   return rev(a) * sigma(a, s) * sigma(a ^ s, b);
 }
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kMaxOps = SQ_NPR_MAX_OPS;
 constexpr int kItemsPerThread = (kMaxOps * 81 + kThreads - 1) / kThreads;
 constexpr int kTri = 136;                  // corner pairs A <= D
 constexpr int kLoadChunks = 4 * 16 * 9 + 32 * 9;
-constexpr size_t kSmemBytes = sizeof(double2) * (kTri * 9 + 4 * 16 * 9 + 2 * 256 * 9);
+constexpr size_t kSmemBytes =
+    sizeof(double2) * (kTri * 9 + 4 * 16 * 9 + 2 * 256 * 9) + sizeof(double) * 2 * 256 * 9;
 
 struct NprOp {
   uint16_t neg1, neg2;  // bit A (C): the entry of row A (C) is -1
@@ -182,7 +184,8 @@ __device__ void path_level(double2 *ut, int n) {
 
 // Step 3: P[X][Y] = G1(X)^dag U_XY G4(Y) and Q[X][Y] = G3(X)^dag U_XY G2(Y),
 // one column of one pair per item.
-__device__ void sandwiches(const double2 *ut, const double2 *gs, double2 *ps, double2 *qs) {
+__device__ void sandwiches(const double2 *ut, const double2 *gs, double2 *ps, double2 *qs,
+                           double *pss, double *qss) {
   for (int it = threadIdx.x; it < 2 * 256 * 3; it += kThreads) {
     const int which = it >= 768;
     const int rem = it - which * 768;
@@ -198,47 +201,63 @@ __device__ void sandwiches(const double2 *ut, const double2 *gs, double2 *ps, do
       for (int k = 0; k < 3; ++k) cmac(h[c], u_elem(ut, x, y, c, k), gr[3 * k + col]);
     }
     double2 *dst = (which ? qs : ps) + pair * 9;
+    double *dsum = (which ? qss : pss) + pair * 9;
 #pragma unroll
     for (int a1 = 0; a1 < 3; ++a1) {
       double2 v = make_double2(0.0, 0.0);
 #pragma unroll
       for (int c = 0; c < 3; ++c) cmac_conj(v, gl[3 * c + a1], h[c]);
       dst[3 * a1 + col] = v;
+      dsum[3 * a1 + col] = v.x + v.y;
     }
   }
 }
 
-// Step 4: output o = 27 a1 + 9 a2 + 3 a3 + a4 of one operator.
-__device__ __forceinline__ double2 contract(const double2 *ps, const double2 *qs, NprOp op,
+// Step 4: output o = 27 a1 + 9 a2 + 3 a3 + a4 of one operator.  The complex
+// products go by the 3M method (Higham, "Stability of a method for
+// multiplying complex matrices with three real matrix multiplications",
+// SIMAX 1992): with re + im of P and Q stored beside them,
+//   sum p q = (T1 - T2) + i (T3 - T1 - T2),
+//   T1 = sum p.re q.re,  T2 = sum p.im q.im,  T3 = sum (p.re + p.im)(q.re + q.im),
+// three real multiply-adds per term instead of four.
+__device__ __forceinline__ double2 contract(const double2 *ps, const double2 *qs,
+                                            const double *pss, const double *qss, NprOp op,
                                             int o) {
   const int a1 = o / 27, a2 = (o / 9) % 3, a3 = (o / 3) % 3, a4 = o % 3;
   const int pe = 3 * a1 + a4, qe = 3 * a3 + a2;
-  double2 acc[4];
+  double t1[4], t2[4], t3[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) acc[k] = make_double2(0.0, 0.0);
+  for (int k = 0; k < 4; ++k) t1[k] = t2[k] = t3[k] = 0.0;
 #pragma unroll 2
   for (int A = 0; A < 16; ++A) {
-    const double2 *qrow = qs + (A ^ op.t1) * 9 + qe;  // Q[C][A ^ t1] at C * 16 * 9
-    const double2 *prow = ps + A * 16 * 9 + pe;       // P[A][D] at D * 9
+    const int qo = (A ^ op.t1) * 9 + qe;  // Q[C][A ^ t1] at qo + C * 16 * 9
+    const int po = A * 16 * 9 + pe;       // P[A][D] at po + D * 9
     const unsigned sa = (op.neg1 >> A) & 1;
 #pragma unroll
     for (int C = 0; C < 16; ++C) {
-      const double2 p = prow[(C ^ op.t2) * 9];
-      const double2 q = qrow[C * 16 * 9];
+      const int pi = po + (C ^ op.t2) * 9, qi = qo + C * 16 * 9;
+      const double2 p = ps[pi], q = qs[qi];
+      const double sp = pss[pi], sq = qss[qi];
       const unsigned neg = sa ^ ((op.neg2 >> C) & 1);
-      cmac(acc[C & 3], make_double2(flip(p.x, neg), flip(p.y, neg)), q);
+      t1[C & 3] = fma(flip(p.x, neg), q.x, t1[C & 3]);
+      t2[C & 3] = fma(flip(p.y, neg), q.y, t2[C & 3]);
+      t3[C & 3] = fma(flip(sp, neg), sq, t3[C & 3]);
     }
   }
-  return make_double2((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x),
-                      (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y));
+  const double T1 = (t1[0] + t1[1]) + (t1[2] + t1[3]);
+  const double T2 = (t2[0] + t2[1]) + (t2[2] + t2[3]);
+  const double T3 = (t3[0] + t3[1]) + (t3[2] + t3[3]);
+  return make_double2(T1 - T2, (T3 - T1) - T2);
 }
 
-__global__ void __launch_bounds__(kThreads, 2) npr_kernel(const NprArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) npr_kernel(const NprArgs a) {
   extern __shared__ double2 smem[];
   double2 *ut = smem;              // [pair A <= D][3][3]
   double2 *gs = ut + kTri * 9;     // [flavour][corner][3][3]
   double2 *ps = gs + 4 * 16 * 9;   // [A][D][a1][a4]
   double2 *qs = ps + 256 * 9;      // [C][B][a3][a2]
+  double *pss = reinterpret_cast<double *>(qs + 256 * 9);  // re + im of ps
+  double *qss = pss + 256 * 9;                             // re + im of qs
   const int tid = threadIdx.x;
   for (int i = tid; i < 16 * 9; i += kThreads) {
     const int c = i / 9, e = i % 9;
@@ -257,14 +276,14 @@ __global__ void __launch_bounds__(kThreads, 2) npr_kernel(const NprArgs a) {
       path_level(ut, n);
       __syncthreads();
     }
-    sandwiches(ut, gs, ps, qs);
+    sandwiches(ut, gs, ps, qs, pss, qss);
     __syncthreads();
     if (h + (int)gridDim.x < a.nhc) issue_loads(a, h + gridDim.x, gs, ut);
 #pragma unroll
     for (int r = 0; r < kItemsPerThread; ++r) {
       const int it = tid + r * kThreads;
       if (it < nitems) {
-        const double2 v = contract(ps, qs, a.ops[it / 81], it % 81);
+        const double2 v = contract(ps, qs, pss, qss, a.ops[it / 81], it % 81);
         if (a.out_hc) a.out_hc[(long)h * nitems + it] = v;
         tot[r].x += v.x;
         tot[r].y += v.y;
