@@ -274,6 +274,71 @@ def solve_full(dims, fat, lng, mass, b, tol, max_iter=100000, t_sign=1):
     return x_e_full + embed_half(dims, 1, x_o), it
 
 
+def bicgstab_full(dims, fat, lng, mass, b, tol, max_iter=100000, t_sign=1):
+    """Solve (m + D) x = b on the whole lattice by BiCGstab (van der Vorst,
+    SIAM J. Sci. Stat. Comput. 13 (1992) 631), the BiCG-family solver the
+    paper names among QUDA's inverters (Sec. 3), applied to the
+    non-Hermitian staggered matrix itself.  Textbook recurrences, x0 = 0,
+    shadow residual r^ = r0, complex scalars:
+      rho = <r^, r>; beta = (rho / rho_old)(alpha / omega);
+      p = r + beta (p - omega v); v = M p; alpha = rho / <r^, v>;
+      s = r - alpha v; t = M s; omega = <t, s> / <t, t>;
+      x += alpha p + omega s; r = s - omega t.
+    Stops when |r| / |b| <= tol and the recomputed |b - M x| / |b| <= tol;
+    if the recomputed residual is larger, restarts from it.
+    Returns (x (V, 3), iterations, true relative residual)."""
+    b = _c128(b)
+    bn = np.linalg.norm(b)
+    x = np.zeros_like(b)
+    if bn == 0:
+        return x, 0, 0.0
+
+    def matvec(v):
+        return dirac(dims, fat, lng, mass, v, t_sign)
+
+    def vdot(a, c):
+        return complex(np.vdot(a.reshape(-1), c.reshape(-1)))
+
+    r = b.copy()
+    it = 0
+    while it < max_iter:
+        rhat = r.copy()
+        rho_old = alpha = omega = 1.0 + 0j
+        p = np.zeros_like(b)
+        v = np.zeros_like(b)
+        while it < max_iter:
+            rho = vdot(rhat, r)
+            if rho == 0:
+                break
+            beta = (rho / rho_old) * (alpha / omega)
+            p = r + beta * (p - omega * v)
+            v = matvec(p)
+            alpha = rho / vdot(rhat, v)
+            s = r - alpha * v
+            it += 1
+            if np.linalg.norm(s) <= tol * bn:
+                x = x + alpha * p
+                r = s
+                break
+            t = matvec(s)
+            tt = vdot(t, t).real
+            if tt == 0:
+                x = x + alpha * p
+                r = s
+                break
+            omega = vdot(t, s) / tt
+            x = x + alpha * p + omega * s
+            r = s - omega * t
+            rho_old = rho
+            if np.linalg.norm(r) <= tol * bn or omega == 0:
+                break
+        r = b - matvec(x)
+        res = float(np.linalg.norm(r) / bn)
+        if res <= tol:
+            return x, it, res
+    return x, it, float(np.linalg.norm(b - matvec(x)) / bn)
+
+
 def cg_multishift(dims, fat, lng, masses, b_even, tol, max_iter=100000, t_sign=1):
     """Multi-shift CG.  Returns (x (nshift, V/2, 3), iterations, true residuals)."""
     lib = _load()
