@@ -22,12 +22,10 @@ struct M3 {
   double2 e[9];
 };
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 
-// c = op(a) op(b), op = identity or dagger
+// c = op(a) op(b), op = identity or dagger; each complex term is four FMAs
+// into the accumulator (the FP64 units bound these kernels).
 template <bool DA, bool DB>
 __device__ __forceinline__ M3 mul(const M3 &a, const M3 &b) {
   M3 c;
@@ -40,9 +38,10 @@ __device__ __forceinline__ M3 mul(const M3 &a, const M3 &b) {
       for (int k = 0; k < 3; ++k) {
         const double2 x = DA ? cconj(a.e[3 * k + i]) : a.e[3 * i + k];
         const double2 y = DB ? cconj(b.e[3 * j + k]) : b.e[3 * k + j];
-        const double2 p = cmul(x, y);
-        t.x += p.x;
-        t.y += p.y;
+        t.x = fma(x.x, y.x, t.x);
+        t.x = fma(-x.y, y.y, t.x);
+        t.y = fma(x.x, y.y, t.y);
+        t.y = fma(x.y, y.x, t.y);
       }
       c.e[3 * i + j] = t;
     }
