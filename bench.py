@@ -364,6 +364,9 @@ def full_lattice_workload(ctx, sq, stream, fat, lng):
     b = torch.from_numpy(g[..., 0] + 1j * g[..., 1]).cuda()
     ctx.cg_solve_full(gid, b, MASS, TOL, stream=stream)
     ms, (x, st) = timed(lambda: ctx.cg_solve_full(gid, b, MASS, TOL, stream=stream), stream, 2)
+    # BiCGstab on M = m + D itself, FP64 (the BiCG-family comparison solver)
+    ms_b, (_, stb) = timed(lambda: ctx.bicgstab_solve_full(gid, b, MASS, TOL, stream=stream),
+                           stream, 1)
     ctx.gauge_free(gid)
     thin = torch.from_numpy(synth.thin_links(dims, EPS, GAUGE_SEED)).cuda()
     f, l = torch.empty_like(thin), torch.empty_like(thin)
@@ -384,6 +387,12 @@ def full_lattice_workload(ctx, sq, stream, fat, lng):
                                   'odd sites reconstructed',
                       'ms': round(ms, 3), 'iterations': st['iterations'],
                       'full_true_residual': st['true_residual']},
+            'bicgstab': {'workload': '20^3x64 whole lattice (m + D) x = b, same source, am 0.01, '
+                                     'tol 1e-8: FP64 BiCGstab on M itself',
+                         'ms': round(ms_b, 1), 'iterations': stb['iterations'],
+                         'm_products': 2 * stb['iterations'],
+                         'full_true_residual': stb['true_residual'],
+                         'vs_even_odd_cg': round(ms_b / ms, 1)},
             'fatten_asqtad': {'workload': '20^3x64 thin links (eps 0.25, seed 0) -> asqtad fat '
                                           'links (MILC path set: 1-link, 6 3-link, 24 5-link, '
                                           '48 7-link staples, 6 Lepage) and Naik links, FP64',

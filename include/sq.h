@@ -180,6 +180,22 @@ int gauge_fatten_asqtad(sq_ctx *ctx, const int dims[4], const double *thin_dev,
 int gauge_load_thin(sq_ctx *ctx, const int dims[4], const double *thin, double c1, double c3,
                     double staple_weight, unsigned flags, int *gauge_id);
 
+/* Solve M x = b on the whole lattice, M = m + D, by BiCGstab (van der Vorst,
+ * SIAM J. Sci. Stat. Comput. 13 (1992) 631) applied to M itself -- the
+ * BiCG-family inverter the paper lists beside CG among QUDA's (Sec. 3) -- in
+ * FP64 on the device.  The recursion stops when |r| / |b| <= tol; the FP64
+ * residual b - M x is then recomputed, and the solve restarts from it (a new
+ * shadow residual) unless it is <= tol too.  stats->iterations counts BiCGstab
+ * steps (two M products each), stats->reliable_updates the recomputed
+ * residuals, stats->true_residual the last of them.  M is not Hermitian, and
+ * on staggered spectra (m + i lambda) BiCGstab needs many more products than
+ * the even-odd CG of cg_solve_full; it is here for comparison.
+ * Arrays, flags (SQ_CG_DEVICE_PTRS, SQ_CG_INITIAL_GUESS), max_iter and stream
+ * as cg_solve_full; the precision options are ignored.  Needs the FP64
+ * 18-real links (gauge_load without SQ_GAUGE_NO_F64). */
+int bicgstab_solve_full(sq_ctx *ctx, int gauge_id, const double *src, double mass, double tol,
+                        const sq_cg_opts *opts, double *x, sq_cg_stats *stats);
+
 /* ---- NPR four-fermion operator (Sec. 2, Eq. 1, Fig. 2, Table 3) ---------- */
 
 #define SQ_NPR_MAX_OPS 16

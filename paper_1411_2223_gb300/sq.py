@@ -98,6 +98,8 @@ SIGNATURES = {
                                  ctypes.POINTER(CgStats)]),
     'cg_solve_full': (_I, [_P, _I, _P, _D, _D, ctypes.POINTER(CgOpts), _P,
                            ctypes.POINTER(CgStats)]),
+    'bicgstab_solve_full': (_I, [_P, _I, _P, _D, _D, ctypes.POINTER(CgOpts), _P,
+                                 ctypes.POINTER(CgStats)]),
     'dirac_apply': (_I, [_P, _I, _D, _P, _P, _P]),
     'serve_submit': (_I, [_P, _I, _P, _D, _D, ctypes.POINTER(_U64)]),
     'serve_poll': (_I, [_P, _U64, _P, ctypes.POINTER(CgStats), _I]),
@@ -407,6 +409,33 @@ class Context:
             _check(status, 'cg_solve_full')
         return x, st.as_dict()
 
+    def bicgstab_solve_full(self, gauge_id, src, mass, tol, max_iter=100000, x0=None,
+                            stream=None, check=True):
+        """Solve (m + D) x = src on the whole lattice by FP64 BiCGstab on M
+        itself.  Arrays as cg_solve_full.  Returns (x, stats dict)."""
+        dev = _is_device(src)
+        if dev:
+            s = src.contiguous()
+            x = s.new_zeros(s.shape)
+        else:
+            s = np.ascontiguousarray(src, dtype=np.complex128)
+            x = np.zeros_like(s)
+        flags = CG_DEVICE_PTRS if dev else 0
+        if x0 is not None:
+            flags |= CG_INITIAL_GUESS
+            if dev:
+                x.copy_(x0)
+            else:
+                x[...] = np.asarray(x0)
+        o = self._opts('f64', 18, -1.0, max_iter, 16, flags, stream)
+        st = CgStats()
+        status = self._lib.bicgstab_solve_full(self.handle, gauge_id, _ptr(s), float(mass),
+                                               float(tol), ctypes.byref(o), _ptr(x),
+                                               ctypes.byref(st))
+        if check:
+            _check(status, 'bicgstab_solve_full')
+        return x, st.as_dict()
+
     def dirac_apply(self, gauge_id, mass, in_dev, out_dev, stream=None):
         """out = (m + D) in on the whole lattice, FP64, device (V, 3) complex128."""
         _check(self._lib.dirac_apply(self.handle, gauge_id, float(mass), _ptr(in_dev),
@@ -486,7 +515,8 @@ def _forward(name):
 
 
 for _n in ('gauge_load', 'gauge_free', 'gauge_fatten', 'gauge_load_thin', 'gauge_fatten_asqtad', 'dslash_apply', 'mdagm_apply', 'cg_solve',
-           'cg_solve_multi', 'cg_solve_multishift', 'cg_solve_full', 'dirac_apply',
+           'cg_solve_multi', 'cg_solve_multishift', 'cg_solve_full', 'bicgstab_solve_full',
+           'dirac_apply',
            'npr_four_fermion', 'serve_submit', 'serve_poll',
            'serve_cancel', 'serve_stats', 'serve_configure'):
     globals()[_n] = _forward(_n)
