@@ -374,9 +374,11 @@ def full_lattice_workload(ctx, sq, stream, fat, lng):
     ms_f, _ = timed(lambda: ctx.gauge_fatten(dims, thin, f, l, stream=stream), stream, 5)
     ctx.gauge_fatten_asqtad(dims, thin, f, l, stream=stream)
     ms_a, _ = timed(lambda: ctx.gauge_fatten_asqtad(dims, thin, f, l, stream=stream), stream, 2)
-    # asqtad: 6 x 2 + 24 x 4 + 48 x 6 + 6 x 4 products for the fat link, 2
-    # for the Naik link (216 flops each), 85 scaled adds of 18 reals
-    flops_a = 4 * vol * (422 * 216 + 85 * 36)
+    # asqtad by nested staple fields: 2 SU(3) products per staple, 6 three-
+    # link, 6 Lepage, 24 five-link and 48 seven-link staples, 2 for the Naik
+    # link (216 flops each); 60 scaled accumulations of 18 reals (36 flops),
+    # 24 sums of two seven-link staples (18) and the one-link term (18)
+    flops_a = 4 * vol * (170 * 216 + 60 * 36 + 24 * 18 + 18)
     # flops per link: 6 staples x 2 products + Naik 2 products, 3x3 complex
     # product = 27 complex multiply-adds = 216 real flops; plus the sums
     flops = 4 * vol * (14 * 216 + 6 * 18 + 36)
@@ -395,7 +397,8 @@ def full_lattice_workload(ctx, sq, stream, fat, lng):
                          'vs_even_odd_cg': round(ms_b / ms, 1)},
             'fatten_asqtad': {'workload': '20^3x64 thin links (eps 0.25, seed 0) -> asqtad fat '
                                           'links (MILC path set: 1-link, 6 3-link, 24 5-link, '
-                                          '48 7-link staples, 6 Lepage) and Naik links, FP64',
+                                          '48 7-link staples, 6 Lepage, built as nested staple '
+                                          'fields) and Naik links, FP64',
                               'ms': round(ms_a, 3),
                               'gflops_fp64': round(flops_a / (ms_a * 1e-3) / 1e9, 1),
                               'frac_of_fp64_peak': round(flops_a / (ms_a * 1e-3) / 1e12 / peak,

@@ -134,65 +134,85 @@ __global__ void __launch_bounds__(128) fatten_kernel(FatGeom g, const double2 *u
 //   5-staple  (r rho)(s nu) mu (-s nu)(-r rho)
 //   7-staple  (q sg)(r rho)(s nu) mu (-s nu)(-r rho)(-q sg)
 //   Lepage    (s nu)(s nu) mu (-s nu)(-s nu)
-// A hop +d at y multiplies by U_d(y), a hop -d by U_d(y - d)^dag.  One thread
-// per (site, direction) walks every path; about 420 SU(3) products a link.
+// A hop +d at y multiplies by U_d(y), a hop -d by U_d(y - d)^dag.
+//
+// Every longer path is a staple around a shorter one, so the paths are built
+// as whole-lattice fields, each level from the one before:
+//   S3 = St_{s nu}[U_mu],  Lepage = St_{s nu}[S3],  S5 = St_{r rho}[S3],
+//   S7 = St_{q sg}[S5],
+//   St_{s nu}[W](x) = h(x) W(x + s nu) h(x + mu)^dag,
+//   h(y) = U_nu(y) (s = +1) or U_nu(y - nu)^dag (s = -1),
+// two SU(3) products per staple: 168 per link for the fat link instead of
+// 422 for every path multiplied out on its own.  One kernel per staple
+// field, one thread per site; S3 and S5 live in device scratch.
 
-struct Walker {
-  const FatGeom &g;
-  const double2 *u;
-  int c[4];
-  long pos;
-  __device__ Walker(const FatGeom &g_, const double2 *u_, const int c0[4], long x)
-      : g(g_), u(u_), pos(x) {
-    for (int k = 0; k < 4; ++k) c[k] = c0[k];
-  }
-  __device__ __forceinline__ void move(int d, int s) {
-    int v = c[d] + s;
-    v = (v < 0) ? v + g.L[d] : (v >= g.L[d] ? v - g.L[d] : v);
-    pos += (long)(v - c[d]) * g.st[d];
-    c[d] = v;
-  }
-  // the link matrix of hop (d, s) from the current position; moves
-  __device__ __forceinline__ M3 hop(int d, int s) {
-    if (s > 0) {
-      const M3 l = load_link(u, pos, d);
-      move(d, 1);
-      return l;
-    }
-    move(d, -1);
-    const M3 l = load_link(u, pos, d);
-    M3 t;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) t.e[3 * i + j] = cconj(l.e[3 * j + i]);
-    return t;
-  }
+struct StapleArgs {
+  FatGeom g;
+  const double2 *u;   // thin links [site][4][9]
+  const double2 *w;   // the extended link W(y) at w + y * w_stride
+  long w_stride;      // 36 (a direction of the links) or 9 (a field)
+  int mu, nu, s;
+  int both;           // add St of s and of -s (the two closings of one S5)
+  double c;
+  double2 *acc;       // acc(x) at acc + x * 36 (the fat link of direction mu)
+  double2 *out;       // St(x) at out + x * 9, or null
 };
 
-// Product along a path of n hops (dirs/signs) starting at site x.
-__device__ M3 path_product(const FatGeom &g, const double2 *u, const int c0[4], long x,
-                           const int *dirs, const int *signs, int n) {
-  Walker w(g, u, c0, x);
-  M3 m = w.hop(dirs[0], signs[0]);
-  for (int k = 1; k < n; ++k) m = mul<false, false>(m, w.hop(dirs[k], signs[k]));
-  return m;
-}
-
-__device__ __forceinline__ void add_scaled(M3 &acc, double c, const M3 &m) {
+__global__ void __launch_bounds__(128) staple_kernel(StapleArgs a) {
+  const long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= a.g.vol) return;
+  int c[4];
+  {
+    long r = x;
+    c[0] = (int)(r % a.g.L[0]); r /= a.g.L[0];
+    c[1] = (int)(r % a.g.L[1]); r /= a.g.L[1];
+    c[2] = (int)(r % a.g.L[2]);
+    c[3] = (int)(r / a.g.L[2]);
+  }
+  const long xpm = shift(a.g, x, c, a.mu, 1);
+  int cm[4] = {c[0], c[1], c[2], c[3]};
+  cm[a.mu] = (c[a.mu] + 1 == a.g.L[a.mu]) ? 0 : c[a.mu] + 1;
+  M3 sum;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) sum.e[e] = make_double2(0.0, 0.0);
+  for (int k = 0; k < (a.both ? 2 : 1); ++k) {
+    const int s = k ? -a.s : a.s;
+    const long xs = shift(a.g, x, c, a.nu, s);     // x + s nu
+    M3 w;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) w.e[e] = __ldg(a.w + xs * a.w_stride + e);
+    M3 t;
+    if (s > 0) {  // U_nu(x) W(x + nu) U_nu(x + mu)^dag
+      t = mul<false, true>(mul<false, false>(load_link(a.u, x, a.nu), w),
+                           load_link(a.u, xpm, a.nu));
+    } else {      // U_nu(x - nu)^dag W(x - nu) U_nu(x - nu + mu)
+      const long xmnpm = shift(a.g, xpm, cm, a.nu, -1);
+      t = mul<false, false>(mul<true, false>(load_link(a.u, xs, a.nu), w),
+                            load_link(a.u, xmnpm, a.nu));
+    }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      sum.e[e].x += t.e[e].x;
+      sum.e[e].y += t.e[e].y;
+    }
+  }
+  if (a.out != nullptr) {
+    double2 *o = a.out + x * 9;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) o[e] = sum.e[e];
+  }
+  double2 *f = a.acc + x * 36;
 #pragma unroll
   for (int e = 0; e < 9; ++e) {
-    acc.e[e].x = fma(c, m.e[e].x, acc.e[e].x);
-    acc.e[e].y = fma(c, m.e[e].y, acc.e[e].y);
+    const double2 v = f[e];
+    f[e] = make_double2(fma(a.c, sum.e[e].x, v.x), fma(a.c, sum.e[e].y, v.y));
   }
 }
 
-struct AsqtadCoeffs {
-  double one, three, five, seven, lepage, naik;
-};
-
-__global__ void __launch_bounds__(128) asqtad_kernel(FatGeom g, const double2 *u, AsqtadCoeffs k,
-                                                     double2 *fat, double2 *lng) {
+// fat = c_one U (every direction); lng = c_N U_mu(x) U_mu(x+mu) U_mu(x+2mu)
+__global__ void __launch_bounds__(128) one_link_naik_kernel(FatGeom g, const double2 *u,
+                                                            double c_one, double c_naik,
+                                                            double2 *fat, double2 *lng) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= 4 * g.vol) return;
   const long x = idx >> 2;
@@ -205,55 +225,20 @@ __global__ void __launch_bounds__(128) asqtad_kernel(FatGeom g, const double2 *u
     c[2] = (int)(r % g.L[2]);
     c[3] = (int)(r / g.L[2]);
   }
-  M3 acc;
-  {
-    const M3 l = load_link(u, x, mu);
-#pragma unroll
-    for (int e = 0; e < 9; ++e) acc.e[e] = make_double2(k.one * l.e[e].x, k.one * l.e[e].y);
-  }
-  int dirs[7], signs[7];
-#pragma unroll 1
-  for (int nu = 0; nu < 4; ++nu) {
-    if (nu == mu) continue;
-#pragma unroll 1
-    for (int s = -1; s <= 1; s += 2) {
-      // 3-staple and Lepage
-      dirs[0] = nu; signs[0] = s; dirs[1] = mu; signs[1] = 1; dirs[2] = nu; signs[2] = -s;
-      add_scaled(acc, k.three, path_product(g, u, c, x, dirs, signs, 3));
-      dirs[0] = nu; signs[0] = s; dirs[1] = nu; signs[1] = s; dirs[2] = mu; signs[2] = 1;
-      dirs[3] = nu; signs[3] = -s; dirs[4] = nu; signs[4] = -s;
-      add_scaled(acc, k.lepage, path_product(g, u, c, x, dirs, signs, 5));
-#pragma unroll 1
-      for (int rho = 0; rho < 4; ++rho) {
-        if (rho == mu || rho == nu) continue;
-#pragma unroll 1
-        for (int r = -1; r <= 1; r += 2) {
-          dirs[0] = rho; signs[0] = r; dirs[1] = nu; signs[1] = s; dirs[2] = mu; signs[2] = 1;
-          dirs[3] = nu; signs[3] = -s; dirs[4] = rho; signs[4] = -r;
-          add_scaled(acc, k.five, path_product(g, u, c, x, dirs, signs, 5));
-          const int sg = 6 - mu - nu - rho;  // the fourth direction
-#pragma unroll 1
-          for (int q = -1; q <= 1; q += 2) {
-            dirs[0] = sg; signs[0] = q; dirs[1] = rho; signs[1] = r; dirs[2] = nu; signs[2] = s;
-            dirs[3] = mu; signs[3] = 1; dirs[4] = nu; signs[4] = -s; dirs[5] = rho;
-            signs[5] = -r; dirs[6] = sg; signs[6] = -q;
-            add_scaled(acc, k.seven, path_product(g, u, c, x, dirs, signs, 7));
-          }
-        }
-      }
-    }
-  }
+  const M3 l = load_link(u, x, mu);
   double2 *f = fat + idx * 9;
 #pragma unroll
-  for (int e = 0; e < 9; ++e) f[e] = acc.e[e];
-  dirs[0] = dirs[1] = dirs[2] = mu;
-  signs[0] = signs[1] = signs[2] = 1;
-  const M3 n = path_product(g, u, c, x, dirs, signs, 3);
-  double2 *l = lng + idx * 9;
+  for (int e = 0; e < 9; ++e) f[e] = make_double2(c_one * l.e[e].x, c_one * l.e[e].y);
+  const M3 n = mul<false, false>(mul<false, false>(l, load_link(u, shift(g, x, c, mu, 1), mu)),
+                                 load_link(u, shift(g, x, c, mu, 2), mu));
+  double2 *o = lng + idx * 9;
 #pragma unroll
-  for (int e = 0; e < 9; ++e) l[e] = make_double2(k.naik * n.e[e].x, k.naik * n.e[e].y);
+  for (int e = 0; e < 9; ++e) o[e] = make_double2(c_naik * n.e[e].x, c_naik * n.e[e].y);
 }
 
+struct AsqtadCoeffs {
+  double one, three, five, seven, lepage, naik;
+};
 
 int launch_fatten(const int dims[4], long vol, const double *thin, double c1, double c3, double w,
                   double *fat, double *lng, cudaStream_t st) {
@@ -312,12 +297,48 @@ extern "C" int gauge_fatten_asqtad(sq_ctx *ctx, const int dims[4], const double 
   cudaSetDevice(ctx->device);
   cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
   const AsqtadCoeffs k{coeffs[0], coeffs[1], coeffs[2], coeffs[3], coeffs[4], coeffs[5]};
-  const long n = 4 * vol;
-  asqtad_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
-      make_fat_geom(dims, vol), reinterpret_cast<const double2 *>(thin_dev), k,
-      reinterpret_cast<double2 *>(fat_dev), reinterpret_cast<double2 *>(lng_dev));
+  const FatGeom g = make_fat_geom(dims, vol);
+  const double2 *u = reinterpret_cast<const double2 *>(thin_dev);
+  double2 *fat = reinterpret_cast<double2 *>(fat_dev);
+  one_link_naik_kernel<<<(unsigned)((4 * vol + 127) / 128), 128, 0, st>>>(
+      g, u, k.one, k.naik, fat, reinterpret_cast<double2 *>(lng_dev));
   SQ_CUDA_TRY(cudaGetLastError());
-  ctx->launches++;
+  uint64_t launches = 1;
+  void *scratch = nullptr;  // S3 and S5 fields, stream-ordered
+  SQ_CUDA_TRY(cudaMallocAsync(&scratch, sizeof(double2) * 18 * (size_t)vol, st));
+  double2 *s3 = static_cast<double2 *>(scratch), *s5 = s3 + 9 * vol;
+  const unsigned blocks = (unsigned)((vol + 127) / 128);
+  cudaError_t e = cudaSuccess;
+  auto staple = [&](const double2 *w, long w_stride, int mu, int nu, int s, int both, double c,
+                    double2 *out) {
+    if (e != cudaSuccess) return;
+    StapleArgs a{g, u, w, w_stride, mu, nu, s, both, c, fat + mu * 9, out};
+    staple_kernel<<<blocks, 128, 0, st>>>(a);
+    e = cudaGetLastError();
+    ++launches;
+  };
+  for (int mu = 0; mu < 4; ++mu)
+    for (int nu = 0; nu < 4; ++nu) {
+      if (nu == mu) continue;
+      for (int s = -1; s <= 1; s += 2) {
+        staple(u + mu * 9, 36, mu, nu, s, 0, k.three, s3);   // 3-staple
+        staple(s3, 9, mu, nu, s, 0, k.lepage, nullptr);     // Lepage
+        for (int rho = 0; rho < 4; ++rho) {
+          if (rho == mu || rho == nu) continue;
+          for (int r = -1; r <= 1; r += 2) {
+            staple(s3, 9, mu, rho, r, 0, k.five, s5);       // 5-staple
+            const int sg = 6 - mu - nu - rho;
+            staple(s5, 9, mu, sg, -1, 1, k.seven, nullptr);  // both 7-staples
+          }
+        }
+      }
+    }
+  cudaFreeAsync(scratch, st);
+  ctx->launches += launches;
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "asqtad staple kernels", __FILE__, __LINE__);
+    return SQ_ERR_CUDA;
+  }
   return SQ_OK;
 }
 
