@@ -65,6 +65,8 @@ def parse_args():
     p.add_argument('--npr-only', action='store_true',
                    help='profiling aid: only run the NPR four-fermion workload')
     p.add_argument('--npr-reps', type=int, default=3)
+    p.add_argument('--fatten-only', action='store_true',
+                   help='profiling aid: only time the two GPU link fattenings (--dims)')
     return p.parse_args()
 
 
@@ -351,23 +353,14 @@ def fp64_peak_tflops():
     return 2.0 * n ** 3 / best / 1e12
 
 
-def full_lattice_workload(ctx, sq, stream, fat, lng):
-    """The whole-lattice solve (m + D) x = b at 20^3 x 64 and the GPU link
-    fattening of the same lattice's thin links."""
+def fatten_workload(ctx, stream, dims=DIMS):
+    """The two GPU link fattenings of the lattice's thin links (eps 0.25,
+    seed 0): the workloads' recipe and MILC's asqtad path set, FP64."""
     import numpy as np
     import torch
     import synth
-    dims = DIMS
     vol = int(np.prod(dims))
-    gid = ctx.gauge_load(dims, fat, lng, flags=sq.GAUGE_NO_I16 | sq.GAUGE_NO_LONG12)
-    g = np.random.default_rng(SRC_SEED).standard_normal((vol, 3, 2))
-    b = torch.from_numpy(g[..., 0] + 1j * g[..., 1]).cuda()
-    ctx.cg_solve_full(gid, b, MASS, TOL, stream=stream)
-    ms, (x, st) = timed(lambda: ctx.cg_solve_full(gid, b, MASS, TOL, stream=stream), stream, 2)
-    # BiCGstab on M = m + D itself, FP64 (the BiCG-family comparison solver)
-    ms_b, (_, stb) = timed(lambda: ctx.bicgstab_solve_full(gid, b, MASS, TOL, stream=stream),
-                           stream, 1)
-    ctx.gauge_free(gid)
+    lat = 'x'.join(map(str, dims))
     thin = torch.from_numpy(synth.thin_links(dims, EPS, GAUGE_SEED)).cuda()
     f, l = torch.empty_like(thin), torch.empty_like(thin)
     ctx.gauge_fatten(dims, thin, f, l, stream=stream)
@@ -384,6 +377,40 @@ def full_lattice_workload(ctx, sq, stream, fat, lng):
     flops = 4 * vol * (14 * 216 + 6 * 18 + 36)
     peak = fp64_peak_tflops()
     gfl = flops / (ms_f * 1e-3) / 1e9
+    return {'fatten_asqtad': {'workload': '%s thin links (eps 0.25, seed 0) -> asqtad fat '
+                                          'links (MILC path set: 1-link, 6 3-link, 24 5-link, '
+                                          '48 7-link staples, 6 Lepage, built as nested staple '
+                                          'fields) and Naik links, FP64' % lat,
+                              'ms': round(ms_a, 3),
+                              'gflops_fp64': round(flops_a / (ms_a * 1e-3) / 1e9, 1),
+                              'frac_of_fp64_peak': round(flops_a / (ms_a * 1e-3) / 1e12 / peak,
+                                                         4)},
+            'fatten': {'workload': '%s thin links (eps 0.25, seed 0) -> fat (6 staples) and '
+                                   'long links, FP64' % lat,
+                       'ms': round(ms_f, 3), 'gflops_fp64': round(gfl, 1),
+                       'roofline': {'bound': 'alu', 'achieved': round(gfl / 1e3, 4),
+                                    'peak': round(peak, 4), 'unit': 'TFLOP/s',
+                                    'frac': round(gfl / 1e3 / peak, 4),
+                                    'peak_kind': 'measured FP64 DGEMM (torch.matmul 4096^3)'}}}
+
+
+def full_lattice_workload(ctx, sq, stream, fat, lng):
+    """The whole-lattice solve (m + D) x = b at 20^3 x 64 (even-odd CG, and
+    BiCGstab for comparison) and the GPU link fattening of the same lattice's
+    thin links."""
+    import numpy as np
+    import torch
+    dims = DIMS
+    vol = int(np.prod(dims))
+    gid = ctx.gauge_load(dims, fat, lng, flags=sq.GAUGE_NO_I16 | sq.GAUGE_NO_LONG12)
+    g = np.random.default_rng(SRC_SEED).standard_normal((vol, 3, 2))
+    b = torch.from_numpy(g[..., 0] + 1j * g[..., 1]).cuda()
+    ctx.cg_solve_full(gid, b, MASS, TOL, stream=stream)
+    ms, (x, st) = timed(lambda: ctx.cg_solve_full(gid, b, MASS, TOL, stream=stream), stream, 2)
+    # BiCGstab on M = m + D itself, FP64 (the BiCG-family comparison solver)
+    ms_b, (_, stb) = timed(lambda: ctx.bicgstab_solve_full(gid, b, MASS, TOL, stream=stream),
+                           stream, 1)
+    ctx.gauge_free(gid)
     return {'solve': {'workload': '20^3x64 whole lattice (m + D) x = b, Gaussian source (seed 0), '
                                   'am 0.01, tol 1e-8: even-site FP32 CG + FP64 reliable updates, '
                                   'odd sites reconstructed',
@@ -395,21 +422,7 @@ def full_lattice_workload(ctx, sq, stream, fat, lng):
                          'm_products': 2 * stb['iterations'],
                          'full_true_residual': stb['true_residual'],
                          'vs_even_odd_cg': round(ms_b / ms, 1)},
-            'fatten_asqtad': {'workload': '20^3x64 thin links (eps 0.25, seed 0) -> asqtad fat '
-                                          'links (MILC path set: 1-link, 6 3-link, 24 5-link, '
-                                          '48 7-link staples, 6 Lepage, built as nested staple '
-                                          'fields) and Naik links, FP64',
-                              'ms': round(ms_a, 3),
-                              'gflops_fp64': round(flops_a / (ms_a * 1e-3) / 1e9, 1),
-                              'frac_of_fp64_peak': round(flops_a / (ms_a * 1e-3) / 1e12 / peak,
-                                                         4)},
-            'fatten': {'workload': '20^3x64 thin links (eps 0.25, seed 0) -> fat (6 staples) and '
-                                   'long links, FP64',
-                       'ms': round(ms_f, 3), 'gflops_fp64': round(gfl, 1),
-                       'roofline': {'bound': 'alu', 'achieved': round(gfl / 1e3, 4),
-                                    'peak': round(peak, 4), 'unit': 'TFLOP/s',
-                                    'frac': round(gfl / 1e3 / peak, 4),
-                                    'peak_kind': 'measured FP64 DGEMM (torch.matmul 4096^3)'}}}
+            **fatten_workload(ctx, stream, dims)}
 
 
 # Flops of one hypercube of the NPR operator (Eq. 1), counting 8 per complex
@@ -462,7 +475,7 @@ def npr_workload(ctx, stream, dims=DIMS, reps=3):
     return res, (dims, links, props, ops)
 
 
-def npr_cpu_baseline(inputs, n_hc=512):
+def npr_cpu_baseline(inputs, n_hc=4096):
     """The oracle's NPR operator on the host cores for the first n_hc
     hypercubes of the workload, scaled to the whole lattice."""
     import oracle
@@ -590,6 +603,12 @@ def main():
     if args.dslash_only and args.dims:
         dims = tuple(int(v) for v in args.dims.split(','))
     vh = int(np.prod(dims)) // 2
+    if args.fatten_only:
+        fdims = tuple(int(v) for v in args.dims.split(',')) if args.dims else DIMS
+        ctx = sq.Context(local)
+        print(json.dumps({'fatten': fatten_workload(ctx, torch.cuda.Stream(), fdims)}))
+        ctx.close()
+        return 0
     if args.npr_only:
         ndims = tuple(int(v) for v in args.dims.split(',')) if args.dims else DIMS
         ctx = sq.Context(local)
