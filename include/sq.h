@@ -37,7 +37,13 @@
  *                          the low half) as excess-32768 integers, then the
  *                          site norm n as an FP32; value = code * n / 32767.
  *           A plane holds `stride` sites (Vh rounded up to a multiple of 64).
- * streams   `void *stream` is a cudaStream_t (NULL: the context's stream).
+ * streams   `void *stream` is a cudaStream_t.  The blocking calls (solves,
+ *           dirac_apply) run on it, or on the context's stream when it is
+ *           NULL or a default stream, after waiting for that stream's work.
+ *           The asynchronous operator calls (dslash_apply, mdagm_apply, the
+ *           pack helpers) run on the context's stream for NULL; the newer
+ *           ones (gauge_fatten*, npr_four_fermion) on the legacy default
+ *           stream for NULL, as CUDA does.
  * errors    every call returns an sq_status; nothing aborts or throws.
  *           Non-finite inputs give SQ_ERR_NONFINITE.
  * ownership the caller owns every pointer it passes; calls that take host
@@ -95,7 +101,8 @@ typedef struct {
     int block_iters;   /* CG iterations per graph launch (default 16)                 */
     unsigned flags;    /* SQ_CG_* */
     void *stream;      /* cudaStream_t the solve runs on (it still returns only when
-                          done); NULL or a default stream: the context's stream     */
+                          done); NULL or a default stream: the context's stream,
+                          after the work already queued on that default stream  */
 } sq_cg_opts;
 
 typedef struct {
@@ -153,7 +160,8 @@ int gauge_free(sq_ctx *ctx, int gauge_id);
  * c1 = 9/8, c3 = -1/24, w = 0.1).  This stands in for the asqtad link
  * fattening that produces the paper's MILC links (Sec. 2, Fig. 1); it is not
  * MILC's full path set.  thin_dev, fat_dev, lng_dev: distinct device arrays
- * in the links layout above.  Asynchronous on `stream`. */
+ * in the links layout above.  Asynchronous on `stream`; NULL means the legacy
+ * default stream (ordered with all other work on it). */
 int gauge_fatten(sq_ctx *ctx, const int dims[4], const double *thin_dev, double c1, double c3,
                  double staple_weight, double *fat_dev, double *lng_dev, void *stream);
 
@@ -168,8 +176,7 @@ int gauge_fatten(sq_ctx *ctx, const int dims[4], const double *thin_dev, double 
  * (a hop +d at y multiplies by U_d(y), a hop -d by U_d(y-d)^dag), the
  * tree-level asqtad values are {5/8, 1/16, 1/64, 1/384, -1/16, -1/24}, which
  * give 9/8 and -1/24 on unit links.  The paper's lattices are MILC asqtad
- * ensembles (Sec. 2, Fig. 1).  Arrays as for gauge_fatten; asynchronous on
- * `stream`. */
+ * ensembles (Sec. 2, Fig. 1).  Arrays and `stream` as for gauge_fatten. */
 int gauge_fatten_asqtad(sq_ctx *ctx, const int dims[4], const double *thin_dev,
                         const double coeffs[6], double *fat_dev, double *lng_dev, void *stream);
 
@@ -229,9 +236,10 @@ int sq_spin_taste(int s, int f, int partner[16], int sign[16]);
  *   out_dev     device, [op][a1][a2][a3][a4] complex128: the sum over z;
  *   out_hc_dev  NULL, or device [z][op][a1][a2][a3][a4] complex128 with
  *               z = z_x + Hx (z_y + Hy (z_z + Hz z_t)), H = L / 2.
- * Device arrays 16-byte aligned; all extents even.  Asynchronous on `stream`
- * (a stream-ordered scratch of 16 * 81 * nops bytes per CTA is taken and
- * returned on it).  The sum over z is deterministic. */
+ * Device arrays 16-byte aligned; all extents even.  Asynchronous on `stream`,
+ * NULL meaning the legacy default stream (a stream-ordered scratch of
+ * 16 * 81 * nops bytes per CTA is taken and returned on it).  The sum over z
+ * is deterministic.  The inputs are not checked for finiteness. */
 int npr_four_fermion(sq_ctx *ctx, const int dims[4], const double *links_dev,
                      const double *const props_dev[4], int nops, const int *ops,
                      double *out_dev, double *out_hc_dev, void *stream);

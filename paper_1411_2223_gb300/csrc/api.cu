@@ -485,7 +485,8 @@ int solve_batch_locked(sq_ctx *ctx, int gauge_id, int nrhs, const double *src,
   cudaStream_t user = (cudaStream_t)o.stream;
   if (user == cudaStreamLegacy || user == cudaStreamPerThread) user = nullptr;
   if (user) st = user;
-  else if (o.stream) SQ_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)o.stream));
+  else  // a default stream (NULL: the legacy one): the caller's work on it first
+    SQ_CUDA_TRY(cudaStreamSynchronize(o.stream ? (cudaStream_t)o.stream : cudaStreamLegacy));
 
   CGWork *w = nullptr;
   SolveCache *cache;
@@ -499,8 +500,8 @@ int solve_batch_locked(sq_ctx *ctx, int gauge_id, int nrhs, const double *src,
   if (!w) {
     int rc = cg_work_create(ctx, gf, o.precision, o.long_recon, nrhs, &w);
     if (rc) return rc;
-    w->cfg_plain = tuned_dslash(ctx, *gf, o.precision, o.long_recon, nrhs, MODE_PLAIN, st);
-    w->cfg_mdagm = tuned_dslash(ctx, *gf, o.precision, o.long_recon, nrhs, MODE_MDAGM, st);
+    w->cfg_norm = tuned_dslash(ctx, *gf, o.precision, o.long_recon, nrhs, MODE_NORM, st);
+    w->cfg_update = tuned_dslash(ctx, *gf, o.precision, o.long_recon, nrhs, MODE_UPDATE, st);
     w->cfg_ru_plain = tuned_dslash(ctx, *gf, PREC_F64, 18, nrhs, MODE_PLAIN, st);
     w->cfg_ru_resid = w->cfg_ru_plain;
     std::lock_guard<std::mutex> lk(g_cache_mu);

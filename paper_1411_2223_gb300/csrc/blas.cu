@@ -1,5 +1,7 @@
-// CG vector kernels (fused axpy / xpay with FP64 norms) and the canonical <->
-// packed colour-vector conversions.  All are bandwidth-bound streaming
+// CG vector kernels (the start r = b, p = r with |b|^2; p = a r + beta p)
+// and the canonical <-> packed colour-vector conversions.  The update
+// xs += alpha p, r -= alpha Ap with |r|^2 runs in the epilogue of the second
+// Dslash (MODE_UPDATE of dslash.cuh).  All are bandwidth-bound streaming
 // kernels: one thread per site, 16-byte accesses, one right-hand side per
 // grid row (blockIdx.y).
 #include "sq_device.cuh"
@@ -11,52 +13,6 @@ namespace sq {
 namespace {
 
 __device__ __forceinline__ bool running(const SlotState *s) { return s->status == SLOT_RUNNING; }
-
-// xs += alpha p ; r -= alpha Ap ; |r|^2 over the row's sites ; the warp that
-// completes the sum runs finish_update for this row's system.
-template <int S>
-__global__ void __launch_bounds__(256, S == PREC_F64 ? 4 : 8) cg_update_kernel(VecArgs a) {
-  using R = typename SpinorIO<S>::R;
-  constexpr int XP = (S == PREC_F64) ? PREC_F64 : PREC_F32;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = blockIdx.y;
-  const int St = a.g.stride;
-  // p, r and xs were last written at least two kernels back: load them
-  // before waiting for the predecessor (which writes Ap and alpha)
-  Vec3<R> p, rv;
-  Vec3<typename SpinorIO<XP>::R> x;
-  if (i < a.g.vh) {
-    p = SpinorIO<S>::load(a.p + r * a.fb, St, i);
-    rv = SpinorIO<S>::load(a.r + r * a.fb, St, i);
-    x = SpinorIO<XP>::load(a.xs + r * a.xs_fb, St, i);
-  }
-  griddep_wait();
-  griddep_launch_dependents();
-  SlotState *s = a.slots + r;
-  if (!running(s)) return;  // the same for every block of the row
-  double val[1] = {0.0};
-  if (i < a.g.vh) {
-    const R al = (R)s->alpha;
-    Vec3<R> ap = SpinorIO<S>::load(a.ap + r * a.fb, St, i);
-    R n2 = 0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      x.c[c].x = fma(al, p.c[c].x, x.c[c].x);
-      x.c[c].y = fma(al, p.c[c].y, x.c[c].y);
-      rv.c[c].x = fma(-al, ap.c[c].x, rv.c[c].x);
-      rv.c[c].y = fma(-al, ap.c[c].y, rv.c[c].y);
-      n2 = fma(rv.c[c].x, rv.c[c].x, fma(rv.c[c].y, rv.c[c].y, n2));
-    }
-    SpinorIO<XP>::store(a.xs + r * a.xs_fb, St, i, x);
-    SpinorIO<S>::store(a.r + r * a.fb, St, i, rv);
-    val[0] = (double)n2;
-  }
-  double *const inst[1] = {a.partial + (size_t)r * red_stride(a.g)};
-  double rr[1];
-  unsigned *tickets = a.counter + (size_t)r * ticket_stride(a.g);
-  if (warp_tree_reduce<1>(val, 1, inst, a.g, i, tickets, rr) && (threadIdx.x & 31) == 0)
-    finish_update(s, rr[0], a.checkpoint);
-}
 
 // p = a r + beta p (a complex, 1 except right after a reliable update)
 template <int S>
@@ -178,18 +134,6 @@ inline dim3 grid_for(const Geom &g, int block, int nrhs) {
 }
 
 }  // namespace
-
-int launch_cg_update(int prec, const VecArgs &a, cudaStream_t st) {
-  if (a.g.vh <= 0) return 0;
-  dim3 grid = grid_for(a.g, 256, a.nrhs);
-  switch (prec) {
-    case PREC_F64: if (launch_pdl(cg_update_kernel<PREC_F64>, grid, dim3(256), 0, st, a)) return -1; break;
-    case PREC_F32: if (launch_pdl(cg_update_kernel<PREC_F32>, grid, dim3(256), 0, st, a)) return -1; break;
-    case PREC_I16: if (launch_pdl(cg_update_kernel<PREC_I16>, grid, dim3(256), 0, st, a)) return -1; break;
-    default: return -1;
-  }
-  return 0;
-}
 
 int launch_cg_xpay(int prec, const VecArgs &a, cudaStream_t st) {
   if (a.g.vh <= 0) return 0;

@@ -19,6 +19,13 @@
 //               with x = x64 + xs folded into x64 first; r is written in the
 //               sloppy precision OUTP, + partials of |r|^2 and <r, p_sloppy>;
 //               the last block finishes the update
+//   MODE_NORM   out = D in (the CG's D_oe p), + partials of |out|^2 +
+//               m^2 |in|^2 over the own index: that is <p, A p> = |M p|^2
+//               for A = M^dag M restricted to the even sites, since
+//               D_eo = -D_oe^dag; the last warp sets alpha
+//   MODE_UPDATE Ap = m^2 p - D in, not stored: xs += alpha p, r -= alpha Ap
+//               (r is `out`), + partials of |r|^2; the last warp finishes
+//               the CG step (beta, or a reliable-update request)
 // For a reliable update the PLAIN FP64 kernel gathers x64 + xs (the FP64
 // solution plus its sloppy increment since the previous update).
 #pragma once
@@ -28,7 +35,7 @@
 
 namespace sq {
 
-enum DslashMode { MODE_PLAIN = 0, MODE_MDAGM = 1, MODE_RESID = 2 };
+enum DslashMode { MODE_PLAIN = 0, MODE_MDAGM = 1, MODE_RESID = 2, MODE_NORM = 3, MODE_UPDATE = 4 };
 enum Gate { GATE_NONE = 0, GATE_RUNNING = 1, GATE_RU = 2 };
 
 struct DslashArgs {
@@ -60,6 +67,7 @@ struct DslashArgs {
   double *partial;            // [value][rhs][chunk]
   unsigned *counter;
   int gate;
+  int checkpoint;             // UPDATE: a reliable update may be requested now
 };
 
 template <int PREC> struct AccumType { using R = float; };
@@ -382,7 +390,7 @@ dslash_kernel(const DslashArgs a) {
     if (i < g.vh) first.load(a, ls, i);
   }
 
-  constexpr bool kPreP = (MODE == MODE_MDAGM) && NR < 8;  // registers allow it
+  constexpr bool kPreP = (MODE == MODE_MDAGM || MODE == MODE_UPDATE) && NR < 8;
   Vec3<R> pre[kPreP ? NR : 1];
   if constexpr (kPreP) {
 #pragma unroll
@@ -391,6 +399,25 @@ dslash_kernel(const DslashArgs a) {
         pre[r] = SpinorIO<PREC>::load(a.p + (size_t)(r0 + r) * a.p_fb, S, i);
       else
         zero(pre[r]);
+    }
+  }
+  // UPDATE: r and xs were last written three or more kernels back as well
+  // (prefetched where registers allow)
+  constexpr int XP = (PREC == PREC_F64) ? PREC_F64 : PREC_F32;
+  using RX = typename SpinorIO<XP>::R;
+  constexpr bool kPreRX = (MODE == MODE_UPDATE) && NR == 1 && PREC != PREC_F64;  // registers
+  Vec3<R> pre_r[kPreRX ? NR : 1];
+  Vec3<RX> pre_x[kPreRX ? NR : 1];
+  if constexpr (kPreRX) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (i < g.vh && r0 + r < a.nrhs) {
+        pre_r[r] = SpinorIO<PREC>::load(a.out + (size_t)(r0 + r) * a.out_fb, S, i);
+        pre_x[r] = SpinorIO<XP>::load(a.xs + (size_t)(r0 + r) * a.xs_fb, S, i);
+      } else {
+        zero(pre_r[r]);
+        zero(pre_x[r]);
+      }
     }
   }
   griddep_wait();
@@ -517,6 +544,92 @@ dslash_kernel(const DslashArgs a) {
           finish_alpha(a.slots + r0 + r, pap[r]);
           if (a.shifts) finish_shift_alpha(a.slots + r0 + r, a.shifts, a.nshift);
         }
+      }
+    }
+  } else if constexpr (MODE == MODE_NORM) {
+    // t = D p ; partial |t|^2 + m^2 |p|^2 (p at the own index of the input
+    // parity: every input site is counted once)
+    double val[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      val[r] = 0.0;
+      if (valid && active[r]) {
+        Vec3<R> o;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { o.c[c].x = R(0.5) * acc[r].c[c].x; o.c[c].y = R(0.5) * acc[r].c[c].y; }
+        SpinorIO<PREC>::store(a.out + (size_t)(r0 + r) * a.out_fb, S, i, o);
+        const Vec3<R> p = SpinorIO<PREC>::load(a.in + (size_t)(r0 + r) * a.in_fb, S, i);
+        R no = 0, np = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          no = fma(o.c[c].x, o.c[c].x, fma(o.c[c].y, o.c[c].y, no));
+          np = fma(p.c[c].x, p.c[c].x, fma(p.c[c].y, p.c[c].y, np));
+        }
+        val[r] = (double)no + a.slots[r0 + r].m2 * (double)np;
+      }
+    }
+    if (a.slots != nullptr && a.partial != nullptr && any_here) {
+      double *inst[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        inst[r] = a.partial + (size_t)min(r0 + r, a.nrhs - 1) * red_stride(g);
+      double pap[NR];
+      if (warp_tree_reduce<NR>(val, min(NR, a.nrhs - r0), inst, g, i,
+                               a.counter + (size_t)tile * ticket_stride(g), pap) &&
+          (threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          if (active[r]) finish_alpha(a.slots + r0 + r, pap[r]);
+      }
+    }
+  } else if constexpr (MODE == MODE_UPDATE) {
+    // Ap = m^2 p - 1/2 acc ; xs += alpha p ; r -= alpha Ap ; partial |r|^2
+    double val[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      val[r] = 0.0;
+      if (valid && active[r]) {
+        const SlotState *sl = a.slots + r0 + r;
+        const R m2 = (R)sl->m2, al = (R)sl->alpha;
+        Vec3<R> p, rv;
+        Vec3<RX> xv;
+        if constexpr (kPreP) p = pre[r];
+        else p = SpinorIO<PREC>::load(a.p + (size_t)(r0 + r) * a.p_fb, S, i);
+        if constexpr (kPreRX) {
+          rv = pre_r[r];
+          xv = pre_x[r];
+        } else {
+          rv = SpinorIO<PREC>::load(a.out + (size_t)(r0 + r) * a.out_fb, S, i);
+          xv = SpinorIO<XP>::load(a.xs + (size_t)(r0 + r) * a.xs_fb, S, i);
+        }
+        R n2 = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const R apx = fma(m2, p.c[c].x, R(-0.5) * acc[r].c[c].x);
+          const R apy = fma(m2, p.c[c].y, R(-0.5) * acc[r].c[c].y);
+          xv.c[c].x = fma((RX)al, (RX)p.c[c].x, xv.c[c].x);
+          xv.c[c].y = fma((RX)al, (RX)p.c[c].y, xv.c[c].y);
+          rv.c[c].x = fma(-al, apx, rv.c[c].x);
+          rv.c[c].y = fma(-al, apy, rv.c[c].y);
+          n2 = fma(rv.c[c].x, rv.c[c].x, fma(rv.c[c].y, rv.c[c].y, n2));
+        }
+        SpinorIO<XP>::store(a.xs + (size_t)(r0 + r) * a.xs_fb, S, i, xv);
+        SpinorIO<PREC>::store(a.out + (size_t)(r0 + r) * a.out_fb, S, i, rv);
+        val[r] = (double)n2;
+      }
+    }
+    if (a.slots != nullptr && a.partial != nullptr && any_here) {
+      double *inst[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        inst[r] = a.partial + (size_t)min(r0 + r, a.nrhs - 1) * red_stride(g);
+      double rr[NR];
+      if (warp_tree_reduce<NR>(val, min(NR, a.nrhs - r0), inst, g, i,
+                               a.counter + (size_t)tile * ticket_stride(g), rr) &&
+          (threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          if (active[r]) finish_update(a.slots + r0 + r, rr[r], a.checkpoint);
       }
     }
   } else {  // MODE_RESID (PREC == F64)

@@ -18,6 +18,10 @@ int launch_dslash_f32(int recon, int nr, int mode, int outp, const DslashArgs &a
   SQ_K_NR(12, MODE_PLAIN, PREC_F32)
   SQ_K_NR(18, MODE_MDAGM, PREC_F32)
   SQ_K_NR(12, MODE_MDAGM, PREC_F32)
+  SQ_K_NR(18, MODE_NORM, PREC_F32)
+  SQ_K_NR(12, MODE_NORM, PREC_F32)
+  SQ_K_NR(18, MODE_UPDATE, PREC_F32)
+  SQ_K_NR(12, MODE_UPDATE, PREC_F32)
 #undef SQ_K_NR
 #undef SQ_K
   return -1;

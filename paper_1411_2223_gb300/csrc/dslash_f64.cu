@@ -17,6 +17,10 @@ int launch_dslash_f64(int recon, int nr, int mode, int outp, const DslashArgs &a
   SQ_K_NR(12, MODE_PLAIN, PREC_F64)
   SQ_K_NR(18, MODE_MDAGM, PREC_F64)
   SQ_K_NR(12, MODE_MDAGM, PREC_F64)
+  SQ_K_NR(18, MODE_NORM, PREC_F64)
+  SQ_K_NR(12, MODE_NORM, PREC_F64)
+  SQ_K_NR(18, MODE_UPDATE, PREC_F64)
+  SQ_K_NR(12, MODE_UPDATE, PREC_F64)
   SQ_K_NR(18, MODE_RESID, PREC_F64)
   SQ_K_NR(18, MODE_RESID, PREC_F32)
   SQ_K_NR(18, MODE_RESID, PREC_I16)

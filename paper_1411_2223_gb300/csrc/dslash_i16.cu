@@ -17,6 +17,10 @@ int launch_dslash_i16(int recon, int nr, int mode, int outp, const DslashArgs &a
   SQ_K_NR(12, MODE_PLAIN, PREC_I16)
   SQ_K_NR(18, MODE_MDAGM, PREC_I16)
   SQ_K_NR(12, MODE_MDAGM, PREC_I16)
+  SQ_K_NR(18, MODE_NORM, PREC_I16)
+  SQ_K_NR(12, MODE_NORM, PREC_I16)
+  SQ_K_NR(18, MODE_UPDATE, PREC_I16)
+  SQ_K_NR(12, MODE_UPDATE, PREC_I16)
 #undef SQ_K_NR
 #undef SQ_K
   return -1;

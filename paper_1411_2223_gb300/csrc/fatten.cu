@@ -295,7 +295,7 @@ extern "C" int gauge_fatten_asqtad(sq_ctx *ctx, const int dims[4], const double 
   int rc = check_lattice_dims(dims, &vol);
   if (rc) return rc;
   cudaSetDevice(ctx->device);
-  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamLegacy;  // NULL: default stream
   const AsqtadCoeffs k{coeffs[0], coeffs[1], coeffs[2], coeffs[3], coeffs[4], coeffs[5]};
   const FatGeom g = make_fat_geom(dims, vol);
   const double2 *u = reinterpret_cast<const double2 *>(thin_dev);
@@ -353,7 +353,7 @@ extern "C" int gauge_fatten(sq_ctx *ctx, const int dims[4], const double *thin_d
   int rc = check_lattice_dims(dims, &vol);
   if (rc) return rc;
   cudaSetDevice(ctx->device);
-  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamLegacy;  // NULL: default stream
   rc = launch_fatten(dims, vol, thin_dev, c1, c3, staple_weight, fat_dev, lng_dev, st);
   if (rc == SQ_OK) ctx->launches++;
   return rc;

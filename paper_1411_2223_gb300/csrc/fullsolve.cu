@@ -311,7 +311,8 @@ extern "C" int dirac_apply(sq_ctx *ctx, int gauge_id, double mass, const double 
   cudaSetDevice(ctx->device);
   const Geom &g = gf->g;
   cudaStream_t st = pick_stream(ctx, stream);
-  if (st == ctx->stream && stream) SQ_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  if (st == ctx->stream)  // a default stream (NULL: the legacy one): its work first
+    SQ_CUDA_TRY(cudaStreamSynchronize(stream ? (cudaStream_t)stream : cudaStreamLegacy));
   const size_t fb = spinor_bytes(PREC_F64, g.stride);
   FullWork w;
   w.ctx = ctx;
@@ -353,7 +354,8 @@ extern "C" int cg_solve_full(sq_ctx *ctx, int gauge_id, const double *src, doubl
   cudaSetDevice(ctx->device);
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = pick_stream(ctx, o.stream);
-  if (st == ctx->stream && o.stream) SQ_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)o.stream));
+  if (st == ctx->stream)  // a default stream (NULL: the legacy one): its work first
+    SQ_CUDA_TRY(cudaStreamSynchronize(o.stream ? (cudaStream_t)o.stream : cudaStreamLegacy));
 
   const size_t fb = spinor_bytes(PREC_F64, g.stride);
   FullWork w;
@@ -476,7 +478,8 @@ extern "C" int bicgstab_solve_full(sq_ctx *ctx, int gauge_id, const double *src,
   cudaSetDevice(ctx->device);
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = pick_stream(ctx, o.stream);
-  if (st == ctx->stream && o.stream) SQ_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)o.stream));
+  if (st == ctx->stream)  // a default stream (NULL: the legacy one): its work first
+    SQ_CUDA_TRY(cudaStreamSynchronize(o.stream ? (cudaStream_t)o.stream : cudaStreamLegacy));
 
   FullOps ops{ctx, gf, st, tuned_dslash(ctx, *gf, PREC_F64, 18, 1, MODE_PLAIN, st)};
   const size_t fv = 2 * ops.fb();  // one whole-lattice vector

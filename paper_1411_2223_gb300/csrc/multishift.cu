@@ -405,7 +405,8 @@ extern "C" int cg_solve_multishift(sq_ctx *ctx, int gauge_id, const double *src,
   cudaStream_t user = (cudaStream_t)o.stream;
   if (user == cudaStreamLegacy || user == cudaStreamPerThread) user = nullptr;
   if (user) st = user;
-  else if (o.stream) SQ_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)o.stream));
+  else  // a default stream (NULL: the legacy one): the caller's work on it first
+    SQ_CUDA_TRY(cudaStreamSynchronize(o.stream ? (cudaStream_t)o.stream : cudaStreamLegacy));
 
   MsWork *w = nullptr;
   int rc = ms_work_get(ctx, gf, gauge_id, o.precision, o.long_recon, nshift, &w);

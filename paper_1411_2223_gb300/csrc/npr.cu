@@ -363,7 +363,7 @@ extern "C" int npr_four_fermion(sq_ctx *ctx, const int dims[4], const double *li
   for (int mu = 1; mu < 4; ++mu) a.st[mu] = a.st[mu - 1] * dims[mu - 1];
 
   cudaSetDevice(ctx->device);
-  cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamLegacy;  // NULL: default stream
   SQ_CUDA_TRY(cudaFuncSetAttribute(npr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kSmemBytes));
   int per_sm = 0, sms = 0;

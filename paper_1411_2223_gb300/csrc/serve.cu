@@ -154,8 +154,8 @@ bool ServeEngine::step_batch(Batch &b) {
       b.canon = nullptr;
       return false;
     }
-    w->cfg_plain = tuned_dslash(ctx, *b.gf, PREC_F32, 18, slots, MODE_PLAIN, b.st);
-    w->cfg_mdagm = tuned_dslash(ctx, *b.gf, PREC_F32, 18, slots, MODE_MDAGM, b.st);
+    w->cfg_norm = tuned_dslash(ctx, *b.gf, PREC_F32, 18, slots, MODE_NORM, b.st);
+    w->cfg_update = tuned_dslash(ctx, *b.gf, PREC_F32, 18, slots, MODE_UPDATE, b.st);
     w->cfg_ru_plain = tuned_dslash(ctx, *b.gf, PREC_F64, 18, slots, MODE_PLAIN, b.st);
     w->cfg_ru_resid = w->cfg_ru_plain;
     b.w = w;

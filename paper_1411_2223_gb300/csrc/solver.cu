@@ -1,11 +1,14 @@
 // Driver of the batched mixed-precision CG (one system per slot).
 //
-// One iteration is four kernels, gated on device-resident slot state so that
-// no host decision sits inside an iteration:
-//   1. t  = D_oe p                          (sloppy Dslash)
-//   2. Ap = m^2 p - D_eo t, <p, Ap>         (sloppy Dslash + epilogue; alpha)
-//   3. xs += alpha p, r -= alpha Ap, |r|^2  (beta, or flag a reliable update)
-//   4. p = a r + beta p
+// One iteration is three kernels, gated on device-resident slot state so
+// that no host decision sits inside an iteration:
+//   1. t = D_oe p, <p, A p> = m^2 |p|^2 + |t|^2      (sloppy Dslash; alpha)
+//   2. Ap = m^2 p - D_eo t (in registers), xs += alpha p, r -= alpha Ap,
+//      |r|^2                                        (sloppy Dslash + epilogue;
+//                                                    beta, or flag a reliable
+//                                                    update)
+//   3. p = a r + beta p
+// (<p, A p> = |M p|^2 with M p = (m p, D_oe p), as D_eo = -D_oe^dag.)
 // and after every RU_PERIOD-th iteration (a checkpoint) the reliable-update
 // pair, which does work only for flagged slots:
 //   R1. t64 = D_oe (x64 + xs)               (FP64 Dslash)
@@ -28,7 +31,7 @@ CGWork::~CGWork() {
   if (exec) cudaGraphExecDestroy(exec);
   if (slots_h) cudaFreeHost(slots_h);
   if (ctx) {
-    void *bufs[] = {x64, b64, t64, r, p, ap, t, xs, slots_d, partial, counters};
+    void *bufs[] = {x64, b64, t64, r, p, t, xs, slots_d, partial, counters};
     for (void *b : bufs)
       if (b) cudaFree(b);
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -52,10 +55,10 @@ int cg_work_create(sq_ctx *ctx, GaugeField *gf, int prec, int recon, int nrhs, C
   w->partial_stride = (size_t)3 * nrhs * red_stride(g);
   w->counter_stride = (size_t)nrhs * ticket_stride(g);
   size_t sizes[] = {w->f64_fb * nrhs, w->f64_fb * nrhs, w->f64_fb * nrhs, w->fb * nrhs,
-                    w->fb * nrhs,     w->fb * nrhs,     w->fb * nrhs,     w->xs_fb * nrhs,
+                    w->fb * nrhs,     w->fb * nrhs,     w->xs_fb * nrhs,
                     sizeof(SlotState) * nrhs, sizeof(double) * 4 * w->partial_stride,
                     sizeof(unsigned) * 4 * w->counter_stride};
-  char **ptrs[] = {&w->x64, &w->b64, &w->t64, &w->r, &w->p, &w->ap, &w->t, &w->xs};
+  char **ptrs[] = {&w->x64, &w->b64, &w->t64, &w->r, &w->p, &w->t, &w->xs};
   size_t total = 0;
   for (size_t s : sizes) total += s;
   {
@@ -65,15 +68,15 @@ int cg_work_create(sq_ctx *ctx, GaugeField *gf, int prec, int recon, int nrhs, C
   }
   w->ctx = ctx;
   w->bytes = total;
-  for (int k = 0; k < 8; ++k) SQ_CUDA_TRY(cudaMalloc((void **)ptrs[k], sizes[k]));
-  SQ_CUDA_TRY(cudaMalloc((void **)&w->slots_d, sizes[8]));
-  SQ_CUDA_TRY(cudaMalloc((void **)&w->partial, sizes[9]));
-  SQ_CUDA_TRY(cudaMalloc((void **)&w->counters, sizes[10]));
-  SQ_CUDA_TRY(cudaMemset(w->counters, 0, sizes[10]));
-  SQ_CUDA_TRY(cudaMemset(w->partial, 0, sizes[9]));
+  for (int k = 0; k < 7; ++k) SQ_CUDA_TRY(cudaMalloc((void **)ptrs[k], sizes[k]));
+  SQ_CUDA_TRY(cudaMalloc((void **)&w->slots_d, sizes[7]));
+  SQ_CUDA_TRY(cudaMalloc((void **)&w->partial, sizes[8]));
+  SQ_CUDA_TRY(cudaMalloc((void **)&w->counters, sizes[9]));
+  SQ_CUDA_TRY(cudaMemset(w->counters, 0, sizes[9]));
+  SQ_CUDA_TRY(cudaMemset(w->partial, 0, sizes[8]));
   // vectors start zeroed so no kernel reads NaN garbage from padding
-  for (int k = 0; k < 8; ++k) SQ_CUDA_TRY(cudaMemset(*ptrs[k], 0, sizes[k]));
-  SQ_CUDA_TRY(cudaMallocHost((void **)&w->slots_h, sizes[8]));
+  for (int k = 0; k < 7; ++k) SQ_CUDA_TRY(cudaMemset(*ptrs[k], 0, sizes[k]));
+  SQ_CUDA_TRY(cudaMallocHost((void **)&w->slots_h, sizes[7]));
   for (int k = 0; k < nrhs; ++k) {
     std::memset(&w->slots_h[k], 0, sizeof(SlotState));
     w->slots_h[k].status = SLOT_IDLE;
@@ -114,7 +117,6 @@ static VecArgs vec_args(CGWork *w, int region) {
   a.f64_fb = w->f64_fb;
   a.r = w->r;
   a.p = w->p;
-  a.ap = w->ap;
   a.fb = w->fb;
   a.xs = w->xs;
   a.xs_fb = w->xs_fb;
@@ -200,31 +202,36 @@ int cg_enqueue_xpay(CGWork *w, cudaStream_t st) {
 
 int cg_enqueue_iteration(CGWork *w, cudaStream_t st, int checkpoint) {
   int rc;
+  // t = D_oe p, with |t|^2 + m^2 |p|^2 = <p, A p>: alpha
   DslashArgs a = dslash_args(w, w->prec, w->recon, 1);
   a.in = w->p;
   a.in_fb = w->fb;
   a.out = w->t;
   a.out_fb = w->fb;
+  a.partial = w->partial;
+  a.counter = w->counters;
   a.gate = GATE_RUNNING;
-  rc = check_launch(w->ctx, launch_dslash(w->prec, w->recon, w->cfg_plain.nr, MODE_PLAIN,
-                                          w->prec, a, w->cfg_plain.block, st));
+  rc = check_launch(w->ctx, launch_dslash(w->prec, w->recon, w->cfg_norm.nr, MODE_NORM,
+                                          w->prec, a, w->cfg_norm.block, st));
   if (rc) return rc;
+  // Ap = m^2 p - D_eo t in registers: xs += alpha p, r -= alpha Ap, |r|^2: beta
   DslashArgs b = dslash_args(w, w->prec, w->recon, 0);
   b.in = w->t;
   b.in_fb = w->fb;
-  b.out = w->ap;
+  b.out = w->r;
   b.out_fb = w->fb;
   b.p = w->p;
   b.p_fb = w->fb;
-  b.partial = w->partial;
-  b.counter = w->counters;
+  b.xs = w->xs;
+  b.xs_fb = w->xs_fb;
+  b.xs_prec = xs_prec(w->prec);
+  b.partial = w->partial + w->partial_stride;
+  b.counter = w->counters + w->counter_stride;
   b.gate = GATE_RUNNING;
-  rc = check_launch(w->ctx, launch_dslash(w->prec, w->recon, w->cfg_mdagm.nr, MODE_MDAGM,
-                                          w->prec, b, w->cfg_mdagm.block, st));
+  b.checkpoint = checkpoint;
+  rc = check_launch(w->ctx, launch_dslash(w->prec, w->recon, w->cfg_update.nr, MODE_UPDATE,
+                                          w->prec, b, w->cfg_update.block, st));
   if (rc) return rc;
-  VecArgs va = vec_args(w, 1);
-  va.checkpoint = checkpoint;
-  if ((rc = check_launch(w->ctx, launch_cg_update(w->prec, va, st)))) return rc;
   if (checkpoint && (rc = cg_enqueue_ru(w, st))) return rc;
   return cg_enqueue_xpay(w, st);
 }

@@ -96,7 +96,7 @@ struct CGWork {
   int prec = PREC_F32, recon = 18, nrhs = 1;
   size_t f64_fb = 0, fb = 0;
   char *x64 = nullptr, *b64 = nullptr, *t64 = nullptr;
-  char *r = nullptr, *p = nullptr, *ap = nullptr, *t = nullptr;
+  char *r = nullptr, *p = nullptr, *t = nullptr;
   char *xs = nullptr;       // solution increment since the last reliable update
   size_t xs_fb = 0;
   SlotState *slots_d = nullptr, *slots_h = nullptr;
@@ -108,7 +108,7 @@ struct CGWork {
   cudaGraphExec_t exec = nullptr;
   int exec_iters = 0;
   int exec_kernels = 0;       // kernels per replay
-  DslashConfig cfg_plain, cfg_mdagm, cfg_ru_plain, cfg_ru_resid;
+  DslashConfig cfg_norm, cfg_update, cfg_ru_plain, cfg_ru_resid;
 
   ~CGWork();
 };

@@ -45,7 +45,6 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 // Precision of the solution increment for a sloppy precision.
 inline int xs_prec(int prec) { return prec == PREC_F64 ? PREC_F64 : PREC_F32; }
 
-int launch_cg_update(int prec, const VecArgs &a, cudaStream_t st);
 int launch_cg_xpay(int prec, const VecArgs &a, cudaStream_t st);
 int launch_cg_init(int prec, const VecArgs &a, int guess, cudaStream_t st);
 

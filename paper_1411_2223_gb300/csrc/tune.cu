@@ -55,9 +55,11 @@ static void tuner_save(Tuner *t) {
 
 DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon, int nrhs,
                           int mode, cudaStream_t st) {
-  // PLAIN and MDAGM are tuned apart: the reduction epilogue of MDAGM favours
-  // more, smaller blocks per SM.  RESID uses the PLAIN shape.
-  if (mode != MODE_MDAGM) mode = MODE_PLAIN;
+  // PLAIN and the reduction epilogues (MDAGM, NORM, UPDATE) are tuned apart:
+  // a reduction favours more, smaller blocks per SM.  RESID uses the PLAIN
+  // shape.
+  if (mode != MODE_MDAGM && mode != MODE_NORM && mode != MODE_UPDATE) mode = MODE_PLAIN;
+  const bool reduces = mode != MODE_PLAIN;
   DslashConfig def;
   def.block = 256;
   def.nr = nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1;
@@ -74,9 +76,11 @@ DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon
   const Geom &g = gf.g;
   size_t fb = spinor_bytes(prec, g.stride);
   void *in = nullptr, *out = nullptr, *aux = nullptr;
-  // aux: p field, slot states, partial sums and the ticket counter (MDAGM)
+  // aux: p field, slot states, partial sums, the ticket counters and (UPDATE)
+  // the solution increment xs
+  const size_t xs_b = spinor_bytes(xs_prec(prec), g.stride) * nrhs;
   size_t aux_b = fb * nrhs + sizeof(SlotState) * nrhs + sizeof(double) * nrhs * red_stride(g) +
-                 sizeof(unsigned) * nrhs * ticket_stride(g) + 256;
+                 sizeof(unsigned) * nrhs * ticket_stride(g) + 256 + xs_b;
   if (cudaMalloc(&in, fb * nrhs) != cudaSuccess) return def;
   if (cudaMalloc(&out, fb * nrhs) != cudaSuccess || cudaMalloc(&aux, aux_b) != cudaSuccess) {
     cudaFree(in);
@@ -89,13 +93,20 @@ DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon
   SlotState *slots = reinterpret_cast<SlotState *>(auxc + fb * nrhs);
   double *partial = reinterpret_cast<double *>(slots + nrhs);
   unsigned *counter = reinterpret_cast<unsigned *>(partial + (size_t)nrhs * red_stride(g));
-  if (mode == MODE_MDAGM) {
+  // xs at the end, 256-byte aligned: rounding the offset down stays inside
+  // the 256 spare bytes after the counters
+  char *xs = auxc + (aux_b - xs_b) / 256 * 256;
+  if (reduces) {
+    // running systems that the timed launches cannot stop (an UPDATE epilogue
+    // never sees convergence or max_iter)
     std::vector<SlotState> hs(nrhs);
     for (auto &s : hs) {
       std::memset(&s, 0, sizeof(s));
       s.status = SLOT_RUNNING;
       s.m2 = 1e-4;
       s.rr = 1.0;
+      s.tol2b2 = -1.0;
+      s.max_iter = 1 << 30;
     }
     cudaMemcpyAsync(slots, hs.data(), sizeof(SlotState) * nrhs, cudaMemcpyHostToDevice, st);
   }
@@ -113,15 +124,22 @@ DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon
   a.in_fb = a.out_fb = fb;
   a.nrhs = nrhs;
   a.gate = GATE_NONE;
-  if (mode == MODE_MDAGM) {
-    a.out_parity = 0;
-    a.links = gf.link_ptr(prec, recon, 0);
-    a.p = auxc;
-    a.p_fb = fb;
+  if (reduces) {
     a.slots = slots;
     a.partial = partial;
     a.counter = counter;
     a.gate = GATE_RUNNING;
+  }
+  if (mode == MODE_MDAGM || mode == MODE_UPDATE) {
+    a.out_parity = 0;
+    a.links = gf.link_ptr(prec, recon, 0);
+    a.p = auxc;
+    a.p_fb = fb;
+  }
+  if (mode == MODE_UPDATE) {
+    a.xs = xs;
+    a.xs_fb = spinor_bytes(xs_prec(prec), g.stride);
+    a.xs_prec = xs_prec(prec);
   }
   // RHS tiles; the many-RHS tiles (8, 12) exist for the FP32 kernels only
   // (launch_dslash refuses the others and the candidate is skipped)

@@ -452,7 +452,8 @@ class Context:
         complex128 propagators [site][colour][source colour]; ops: list of
         (S1, F1, S2, F2) 4-bit masks; out_dev: (nops, 3, 3, 3, 3) complex128,
         the sum over hypercubes; out_hc_dev: None or (V/16, nops, 3, 3, 3, 3)
-        complex128 per hypercube.  Asynchronous on `stream`."""
+        complex128 per hypercube.  Asynchronous on `stream` (None: the
+        default stream, which torch's default stream is)."""
         d = (ctypes.c_int * 4)(*[int(v) for v in dims])
         if len(props_dev) != 4:
             raise ValueError('four propagators')

@@ -29,7 +29,11 @@ def to_dev(a):
 def packed_buffer(ctx, gid, prec):
     import torch
     nbytes, _ = ctx.spinor_bytes(gid, prec)
-    return torch.zeros(nbytes, dtype=torch.uint8, device='cuda')
+    buf = torch.zeros(nbytes, dtype=torch.uint8, device='cuda')
+    # the library's calls without a stream run on the context's own stream:
+    # the zero fill must be done before they write
+    torch.cuda.synchronize()
+    return buf
 
 
 def pack(ctx, gid, prec, v_half):
