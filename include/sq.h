@@ -95,7 +95,7 @@ typedef struct {
     int precision;     /* sloppy precision: SQ_PREC_F64 = plain FP64 CG (default F32) */
     int long_recon;    /* 18 or 12: long links stored 18-real or 12-real (default 18) */
     double delta;      /* reliable update when |r| < delta * max|r| since the last
-                          one; < 0 (default): 0.01 for FP32, 0.1 for 16-bit sloppy
+                          one; < 0 (default): 0.001 for FP32, 0.1 for 16-bit sloppy
                           vectors; ignored for plain FP64 CG                         */
     int max_iter;      /* default 100000                                              */
     int block_iters;   /* CG iterations per graph launch (default 16)                 */

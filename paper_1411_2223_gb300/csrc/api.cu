@@ -174,7 +174,7 @@ extern "C" void sq_cg_opts_default(sq_cg_opts *o) {
   if (!o) return;
   o->precision = SQ_PREC_F32;
   o->long_recon = 18;
-  o->delta = -1.0;  // precision default: 0.01 (FP32), 0.1 (16-bit)
+  o->delta = -1.0;  // precision default: 0.001 (FP32), 0.1 (16-bit)
   o->max_iter = 100000;
   o->block_iters = 16;
   o->flags = 0;
@@ -467,7 +467,7 @@ int solve_batch_locked(sq_ctx *ctx, int gauge_id, int nrhs, const double *src,
   if (opts_in) o = *opts_in;
   if (o.precision < 0 || o.precision > 2) return SQ_ERR_ARG;
   if (o.long_recon != 18 && o.long_recon != 12) return SQ_ERR_ARG;
-  if (o.delta < 0) o.delta = (o.precision == PREC_I16) ? 0.1 : 0.01;
+  if (o.delta < 0) o.delta = (o.precision == PREC_I16) ? 0.1 : 0.001;
   if (o.max_iter < 1 || o.block_iters < 1 || !(o.delta >= 0) || o.delta >= 1) return SQ_ERR_ARG;
   GaugeField *gf = ctx->gauge(gauge_id);
   if (!gf) return SQ_ERR_NOTFOUND;
