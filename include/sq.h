@@ -205,7 +205,7 @@ int bicgstab_solve_full(sq_ctx *ctx, int gauge_id, const double *src, double mas
 
 /* ---- NPR four-fermion operator (Sec. 2, Eq. 1, Fig. 2, Table 3) ---------- */
 
-#define SQ_NPR_MAX_OPS 16
+#define SQ_NPR_MAX_OPS 16  /* operators per kernel launch */
 
 /* The hypercube spin-taste matrix of Eq. 1,
  *   (gamma_S x xi_F)_{AB} = Tr(gamma_A^dag gamma_S gamma_B gamma_F^dag) / 4,
@@ -218,7 +218,9 @@ int sq_spin_taste(int s, int f, int partner[16], int sign[16]);
 
 /* The one-colour four-fermion operator of the paper's NPR code, Eq. 1, in
  * FP64 on the device, for nops operators (S1, F1, S2, F2) (4-bit masks, host
- * array ops[nops][4], 0 <= nops <= SQ_NPR_MAX_OPS):
+ * array ops[nops][4], 0 <= nops <= 2^20; they are processed SQ_NPR_MAX_OPS at
+ * a time, each group recomputing the averaged links and sandwiches -- about
+ * a sixth of a group's work at 8 operators, less at 16):
  *   O[a1][a2][a3][a4](z) = sum_{A,B,C,D} sum_{c1..c4}
  *       conj(G1(z_A)[c1][a1]) (gamma_S1 x xi_F1)_{AB} G2(z_B)[c2][a2]
  *     * conj(G3(z_C)[c3][a3]) (gamma_S2 x xi_F2)_{CD} G4(z_D)[c4][a4]

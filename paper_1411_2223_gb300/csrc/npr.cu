@@ -78,7 +78,8 @@ struct NprOp {
 struct NprArgs {
   const double2 *links;    // [site][mu][3][3]
   const double2 *prop[4];  // [site][3][3]
-  double2 *out_hc;         // [hypercube][op][81] or null
+  double2 *out_hc;         // this group's first op of [hypercube][op][81], or null
+  long hc_stride;          // elements per hypercube of out_hc (all ops x 81)
   double2 *partial;        // [cta][op][81]
   int H[4];                // hypercubes per direction
   long st[4];              // site strides
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1) npr_kernel(const NprArgs a) {
       const int it = tid + r * kThreads;
       if (it < nitems) {
         const double2 v = contract(ps, qs, pss, qss, a.ops[it / 81], it % 81);
-        if (a.out_hc) a.out_hc[(long)h * nitems + it] = v;
+        if (a.out_hc) a.out_hc[(long)h * a.hc_stride + it] = v;
         tot[r].x += v.x;
         tot[r].y += v.y;
       }
@@ -329,38 +330,27 @@ extern "C" int sq_spin_taste(int s, int f, int partner[16], int sign[16]) {
 extern "C" int npr_four_fermion(sq_ctx *ctx, const int dims[4], const double *links_dev,
                                 const double *const props_dev[4], int nops, const int *ops,
                                 double *out_dev, double *out_hc_dev, void *stream) {
-  if (!ctx || !dims || !links_dev || !props_dev || nops < 0 || nops > kMaxOps) return SQ_ERR_ARG;
+  if (!ctx || !dims || !links_dev || !props_dev || nops < 0 || nops > (1 << 20))
+    return SQ_ERR_ARG;
   if (nops > 0 && (!ops || !out_dev)) return SQ_ERR_ARG;
   long vol;
   int rc = check_lattice_dims(dims, &vol);
   if (rc) return rc;
+  if (!aligned16(links_dev) || !aligned16(out_dev) || !aligned16(out_hc_dev)) return SQ_ERR_ARG;
+  for (int f = 0; f < 4; ++f)
+    if (!props_dev[f] || !aligned16(props_dev[f])) return SQ_ERR_ARG;
+  for (long k = 0; k < 4L * nops; ++k)
+    if (ops[k] < 0 || ops[k] > 15) return SQ_ERR_ARG;
   if (nops == 0) return SQ_OK;
+
   NprArgs a{};
   a.links = reinterpret_cast<const double2 *>(links_dev);
-  if (!aligned16(links_dev) || !aligned16(out_dev) || !aligned16(out_hc_dev)) return SQ_ERR_ARG;
-  for (int f = 0; f < 4; ++f) {
-    if (!props_dev[f] || !aligned16(props_dev[f])) return SQ_ERR_ARG;
-    a.prop[f] = reinterpret_cast<const double2 *>(props_dev[f]);
-  }
-  for (int k = 0; k < nops; ++k) {
-    const int *o = ops + 4 * k;
-    for (int j = 0; j < 4; ++j)
-      if (o[j] < 0 || o[j] > 15) return SQ_ERR_ARG;
-    NprOp &p = a.ops[k];
-    p.t1 = (uint8_t)(o[0] ^ o[1]);
-    p.t2 = (uint8_t)(o[2] ^ o[3]);
-    p.neg1 = p.neg2 = 0;
-    for (int c = 0; c < 16; ++c) {
-      if (spin_taste_sign(o[0], o[1], c) < 0) p.neg1 |= (uint16_t)(1u << c);
-      if (spin_taste_sign(o[2], o[3], c) < 0) p.neg2 |= (uint16_t)(1u << c);
-    }
-  }
-  a.out_hc = reinterpret_cast<double2 *>(out_hc_dev);
-  a.nops = nops;
+  for (int f = 0; f < 4; ++f) a.prop[f] = reinterpret_cast<const double2 *>(props_dev[f]);
   a.nhc = (int)(vol / 16);
   for (int mu = 0; mu < 4; ++mu) a.H[mu] = dims[mu] / 2;
   a.st[0] = 1;
   for (int mu = 1; mu < 4; ++mu) a.st[mu] = a.st[mu - 1] * dims[mu - 1];
+  a.hc_stride = 81L * nops;
 
   cudaSetDevice(ctx->device);
   cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamLegacy;  // NULL: default stream
@@ -372,22 +362,40 @@ extern "C" int npr_four_fermion(sq_ctx *ctx, const int dims[4], const double *li
   SQ_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
   if (per_sm < 1) per_sm = 1;
   const int grid = (int)std::min<long>(a.nhc, (long)per_sm * sms);
-  const int nitems = nops * 81;
   void *partial = nullptr;
-  SQ_CUDA_TRY(cudaMallocAsync(&partial, sizeof(double2) * (size_t)grid * nitems, st));
+  SQ_CUDA_TRY(cudaMallocAsync(&partial, sizeof(double2) * (size_t)grid * kMaxOps * 81, st));
   a.partial = static_cast<double2 *>(partial);
-  npr_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) {
-    npr_sum_kernel<<<(nitems + 255) / 256, 256, 0, st>>>(
-        a.partial, grid, nitems, reinterpret_cast<double2 *>(out_dev));
+  cudaError_t e = cudaSuccess;
+  // kMaxOps operators per launch pair; each group recomputes the averaged
+  // links and the sandwiches P, Q of every hypercube
+  for (int g0 = 0; g0 < nops && e == cudaSuccess; g0 += kMaxOps) {
+    a.nops = std::min(kMaxOps, nops - g0);
+    for (int k = 0; k < a.nops; ++k) {
+      const int *o = ops + 4 * (g0 + k);
+      NprOp &p = a.ops[k];
+      p.t1 = (uint8_t)(o[0] ^ o[1]);
+      p.t2 = (uint8_t)(o[2] ^ o[3]);
+      p.neg1 = p.neg2 = 0;
+      for (int c = 0; c < 16; ++c) {
+        if (spin_taste_sign(o[0], o[1], c) < 0) p.neg1 |= (uint16_t)(1u << c);
+        if (spin_taste_sign(o[2], o[3], c) < 0) p.neg2 |= (uint16_t)(1u << c);
+      }
+    }
+    a.out_hc = out_hc_dev ? reinterpret_cast<double2 *>(out_hc_dev) + 81L * g0 : nullptr;
+    const int nitems = a.nops * 81;
+    npr_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
     e = cudaGetLastError();
+    if (e == cudaSuccess) {
+      npr_sum_kernel<<<(nitems + 255) / 256, 256, 0, st>>>(
+          a.partial, grid, nitems, reinterpret_cast<double2 *>(out_dev) + 81L * g0);
+      e = cudaGetLastError();
+      ctx->launches += 2;
+    }
   }
   cudaFreeAsync(partial, st);
   if (e != cudaSuccess) {
     set_last_cuda_error(e, "npr kernels", __FILE__, __LINE__);
     return SQ_ERR_CUDA;
   }
-  ctx->launches += 2;
   return SQ_OK;
 }

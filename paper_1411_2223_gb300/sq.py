@@ -442,7 +442,7 @@ class Context:
                                      _ptr(out_dev), _stream(stream)), 'dirac_apply')
 
     # ------------------------------------------------- NPR operator (Eq. 1)
-    NPR_MAX_OPS = 16
+    NPR_MAX_OPS = 16   # operators per kernel launch (more are done in groups)
 
     def npr_four_fermion(self, dims, links_dev, props_dev, ops, out_dev, out_hc_dev=None,
                          stream=None):
