@@ -67,6 +67,8 @@ def parse_args():
     p.add_argument('--npr-reps', type=int, default=3)
     p.add_argument('--fatten-only', action='store_true',
                    help='profiling aid: only time the two GPU link fattenings (--dims)')
+    p.add_argument('--batched-only', action='store_true',
+                   help='profiling aid: only run the 24^3x64 multi-RHS / multi-shift workload')
     return p.parse_args()
 
 
@@ -603,6 +605,11 @@ def main():
     if args.dslash_only and args.dims:
         dims = tuple(int(v) for v in args.dims.split(','))
     vh = int(np.prod(dims)) // 2
+    if args.batched_only:
+        ctx = sq.Context(local)
+        print(json.dumps({'batched_24x64': batched_workload(ctx, sq, torch.cuda.Stream())}))
+        ctx.close()
+        return 0
     if args.fatten_only:
         fdims = tuple(int(v) for v in args.dims.split(',')) if args.dims else DIMS
         ctx = sq.Context(local)

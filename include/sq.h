@@ -176,7 +176,10 @@ int gauge_fatten(sq_ctx *ctx, const int dims[4], const double *thin_dev, double 
  * (a hop +d at y multiplies by U_d(y), a hop -d by U_d(y-d)^dag), the
  * tree-level asqtad values are {5/8, 1/16, 1/64, 1/384, -1/16, -1/24}, which
  * give 9/8 and -1/24 on unit links.  The paper's lattices are MILC asqtad
- * ensembles (Sec. 2, Fig. 1).  Arrays and `stream` as for gauge_fatten. */
+ * ensembles (Sec. 2, Fig. 1).  Arrays and `stream` as for gauge_fatten; the
+ * paths are built as nested staple fields in a stream-ordered device scratch
+ * of 288 bytes per site, taken and returned on `stream` (outside the HBM
+ * budget). */
 int gauge_fatten_asqtad(sq_ctx *ctx, const int dims[4], const double *thin_dev,
                         const double coeffs[6], double *fat_dev, double *lng_dev, void *stream);
 
