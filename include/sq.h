@@ -195,7 +195,8 @@ int gauge_load_thin(sq_ctx *ctx, const int dims[4], const double *thin, double c
  * BiCG-family inverter the paper lists beside CG among QUDA's (Sec. 3) -- in
  * FP64 on the device.  The recursion stops when |r| / |b| <= tol; the FP64
  * residual b - M x is then recomputed, and the solve restarts from it (a new
- * shadow residual) unless it is <= tol too.  stats->iterations counts BiCGstab
+ * shadow residual) unless it is <= tol too; it also restarts on a breakdown
+ * (rho = 0 or <r^, v> = 0), at most 64 times in all (then SQ_NOT_CONVERGED).  stats->iterations counts BiCGstab
  * steps (two M products each), stats->reliable_updates the recomputed
  * residuals, stats->true_residual the last of them.  M is not Hermitian, and
  * on staggered spectra (m + i lambda) BiCGstab needs many more products than
