@@ -409,9 +409,12 @@ def full_lattice_workload(ctx, sq, stream, fat, lng):
     b = torch.from_numpy(g[..., 0] + 1j * g[..., 1]).cuda()
     ctx.cg_solve_full(gid, b, MASS, TOL, stream=stream)
     ms, (x, st) = timed(lambda: ctx.cg_solve_full(gid, b, MASS, TOL, stream=stream), stream, 2)
-    # BiCGstab on M = m + D itself, FP64 (the BiCG-family comparison solver)
+    # BiCGstab on M = m + D itself (the BiCG-family comparison solver): FP64,
+    # and FP32 with FP64 reliable updates
     ms_b, (_, stb) = timed(lambda: ctx.bicgstab_solve_full(gid, b, MASS, TOL, stream=stream),
                            stream, 1)
+    ms_bm, (_, stbm) = timed(lambda: ctx.bicgstab_solve_full(gid, b, MASS, TOL, precision='f32',
+                                                             stream=stream), stream, 1)
     ctx.gauge_free(gid)
     return {'solve': {'workload': '20^3x64 whole lattice (m + D) x = b, Gaussian source (seed 0), '
                                   'am 0.01, tol 1e-8: even-site FP32 CG + FP64 reliable updates, '
@@ -424,6 +427,12 @@ def full_lattice_workload(ctx, sq, stream, fat, lng):
                          'm_products': 2 * stb['iterations'],
                          'full_true_residual': stb['true_residual'],
                          'vs_even_odd_cg': round(ms_b / ms, 1)},
+            'bicgstab_mixed': {'workload': 'same system: FP32 BiCGstab on M with FP64 reliable '
+                                           'updates (delta 0.1)',
+                               'ms': round(ms_bm, 1), 'iterations': stbm['iterations'],
+                               'reliable_updates': stbm['reliable_updates'],
+                               'full_true_residual': stbm['true_residual'],
+                               'vs_even_odd_cg': round(ms_bm / ms, 1)},
             **fatten_workload(ctx, stream, dims)}
 
 

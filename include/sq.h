@@ -201,9 +201,14 @@ int gauge_load_thin(sq_ctx *ctx, const int dims[4], const double *thin, double c
  * residuals, stats->true_residual the last of them.  M is not Hermitian, and
  * on staggered spectra (m + i lambda) BiCGstab needs many more products than
  * the even-odd CG of cg_solve_full; it is here for comparison.
- * Arrays, flags (SQ_CG_DEVICE_PTRS, SQ_CG_INITIAL_GUESS), max_iter and stream
- * as cg_solve_full; the precision options are ignored.  Needs the FP64
- * 18-real links (gauge_load without SQ_GAUGE_NO_F64). */
+ * opts->precision: SQ_PREC_F64 runs everything in FP64; SQ_PREC_F32 (the
+ * sq_cg_opts default) keeps the vectors and the Dslash in FP32 and folds the
+ * FP32 solution increment into an FP64 solution at reliable updates, when
+ * |r| < delta max|r| since the last one (opts->delta, < 0: 0.1) or the
+ * recursion claims convergence; r is then the FP64 residual b - M x.  NULL
+ * opts: FP64.  Arrays, flags (SQ_CG_DEVICE_PTRS, SQ_CG_INITIAL_GUESS),
+ * max_iter and stream as cg_solve_full; SQ_ERR_UNSUPPORTED for 16-bit or for
+ * a field without the FP64 (and, for FP32, FP32) 18-real links. */
 int bicgstab_solve_full(sq_ctx *ctx, int gauge_id, const double *src, double mass, double tol,
                         const sq_cg_opts *opts, double *x, sq_cg_stats *stats);
 

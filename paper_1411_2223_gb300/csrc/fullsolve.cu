@@ -51,28 +51,30 @@ __global__ void half_to_full_kernel(Geom g, int parity, const char *half, double
   for (int k = 0; k < 3; ++k) c[k] = v.c[k];
 }
 
-// out = a x + b y + c z on packed FP64 halves (z may be null)
+// out = a x + b y + c z on packed halves of precision P (z may be null)
+template <int P>
 __global__ void lincomb_kernel(Geom g, double a, const char *x, double b, const char *y, double c,
                                const char *z, char *out) {
+  using R = typename SpinorIO<P>::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.vh) return;
-  const Vec3<double> vx = SpinorIO<PREC_F64>::load(x, g.stride, i);
-  const Vec3<double> vy = SpinorIO<PREC_F64>::load(y, g.stride, i);
-  Vec3<double> o;
+  const Vec3<R> vx = SpinorIO<P>::load(x, g.stride, i);
+  const Vec3<R> vy = SpinorIO<P>::load(y, g.stride, i);
+  Vec3<R> o;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    o.c[k].x = fma(a, vx.c[k].x, b * vy.c[k].x);
-    o.c[k].y = fma(a, vx.c[k].y, b * vy.c[k].y);
+    o.c[k].x = fma((R)a, vx.c[k].x, (R)b * vy.c[k].x);
+    o.c[k].y = fma((R)a, vx.c[k].y, (R)b * vy.c[k].y);
   }
   if (z != nullptr) {
-    const Vec3<double> vz = SpinorIO<PREC_F64>::load(z, g.stride, i);
+    const Vec3<R> vz = SpinorIO<P>::load(z, g.stride, i);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      o.c[k].x = fma(c, vz.c[k].x, o.c[k].x);
-      o.c[k].y = fma(c, vz.c[k].y, o.c[k].y);
+      o.c[k].x = fma((R)c, vz.c[k].x, o.c[k].x);
+      o.c[k].y = fma((R)c, vz.c[k].y, o.c[k].y);
     }
   }
-  SpinorIO<PREC_F64>::store(out, g.stride, i, o);
+  SpinorIO<P>::store(out, g.stride, i, o);
 }
 
 // |v|^2 of a packed FP64 half: fixed 128-site chunk partials, then one block
@@ -100,49 +102,65 @@ __global__ void sum_partials_kernel(const double *partial, int n, double *out) {
 // ---- whole-lattice vectors for BiCGstab: [even half][odd half], packed FP64
 // halves of fb bytes each; site i < 2 vh is half i / vh, index i % vh.
 
-__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+template <typename R2>
+__device__ __forceinline__ R2 zmul(R2 a, R2 b) {
+  R2 c;
+  c.x = fma(a.x, b.x, -a.y * b.y);
+  c.y = fma(a.x, b.y, a.y * b.x);
+  return c;
 }
 
-// out = x + a y + b z (complex a, b; z may be null).  With partial: also
-// |out|^2 and <w, out> = sum conj(w) out (w may be null) as 3 rows of chunk
-// partials (nch chunks of the 2 vh sites).
+// out = x + a y + b z (complex a, b; z may be null) on vectors of precision
+// P, arithmetic in P's real type.  With partial: also |out|^2 and
+// <w, out> = sum conj(w) out (w may be null) as 3 rows of chunk partials
+// (nch chunks of the 2 vh sites), accumulated in FP64.
+template <int P>
 __global__ void zaxpy_kernel(Geom g, size_t fb, const char *x, double2 a, const char *y,
                              double2 b, const char *z, char *out, const char *w,
                              double *partial, int nch) {
+  using R = typename SpinorIO<P>::R;
+  using R2 = typename C2<R>::T;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double val[3] = {0.0, 0.0, 0.0};
   if (i < 2 * g.vh) {
     const int half = i >= g.vh;
     const int j = i - half * g.vh;
     const size_t off = half * fb;
-    const Vec3<double> vx = SpinorIO<PREC_F64>::load(x + off, g.stride, j);
-    const Vec3<double> vy = SpinorIO<PREC_F64>::load(y + off, g.stride, j);
-    Vec3<double> o;
+    R2 ar, br;
+    ar.x = (R)a.x; ar.y = (R)a.y;
+    br.x = (R)b.x; br.y = (R)b.y;
+    const Vec3<R> vx = SpinorIO<P>::load(x + off, g.stride, j);
+    const Vec3<R> vy = SpinorIO<P>::load(y + off, g.stride, j);
+    Vec3<R> o;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const double2 t = zmul(a, vy.c[k]);
-      o.c[k] = make_double2(vx.c[k].x + t.x, vx.c[k].y + t.y);
+      const R2 t = zmul(ar, vy.c[k]);
+      o.c[k].x = vx.c[k].x + t.x;
+      o.c[k].y = vx.c[k].y + t.y;
     }
     if (z != nullptr) {
-      const Vec3<double> vz = SpinorIO<PREC_F64>::load(z + off, g.stride, j);
+      const Vec3<R> vz = SpinorIO<P>::load(z + off, g.stride, j);
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const double2 t = zmul(b, vz.c[k]);
+        const R2 t = zmul(br, vz.c[k]);
         o.c[k].x += t.x;
         o.c[k].y += t.y;
       }
     }
-    SpinorIO<PREC_F64>::store(out + off, g.stride, j, o);
+    SpinorIO<P>::store(out + off, g.stride, j, o);
     if (partial != nullptr) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) val[0] = fma(o.c[k].x, o.c[k].x, fma(o.c[k].y, o.c[k].y, val[0]));
+      for (int k = 0; k < 3; ++k) {
+        const double ox = o.c[k].x, oy = o.c[k].y;
+        val[0] = fma(ox, ox, fma(oy, oy, val[0]));
+      }
       if (w != nullptr) {
-        const Vec3<double> vw = SpinorIO<PREC_F64>::load(w + off, g.stride, j);
+        const Vec3<R> vw = SpinorIO<P>::load(w + off, g.stride, j);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          val[1] = fma(vw.c[k].x, o.c[k].x, fma(vw.c[k].y, o.c[k].y, val[1]));
-          val[2] = fma(vw.c[k].x, o.c[k].y, fma(-vw.c[k].y, o.c[k].x, val[2]));
+          const double wx = vw.c[k].x, wy = vw.c[k].y, ox = o.c[k].x, oy = o.c[k].y;
+          val[1] = fma(wx, ox, fma(wy, oy, val[1]));
+          val[2] = fma(wx, oy, fma(-wy, ox, val[2]));
         }
       }
     }
@@ -154,25 +172,59 @@ __global__ void zaxpy_kernel(Geom g, size_t fb, const char *x, double2 a, const 
 }
 
 // |x|^2 and <x, y> = sum conj(x) y over both parities, as 3 rows of partials.
+template <int P>
 __global__ void zdot_kernel(Geom g, size_t fb, const char *x, const char *y, double *partial,
                             int nch) {
+  using R = typename SpinorIO<P>::R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double val[3] = {0.0, 0.0, 0.0};
   if (i < 2 * g.vh) {
     const int half = i >= g.vh;
     const int j = i - half * g.vh;
     const size_t off = half * fb;
-    const Vec3<double> vx = SpinorIO<PREC_F64>::load(x + off, g.stride, j);
-    const Vec3<double> vy = SpinorIO<PREC_F64>::load(y + off, g.stride, j);
+    const Vec3<R> vx = SpinorIO<P>::load(x + off, g.stride, j);
+    const Vec3<R> vy = SpinorIO<P>::load(y + off, g.stride, j);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      val[0] = fma(vx.c[k].x, vx.c[k].x, fma(vx.c[k].y, vx.c[k].y, val[0]));
-      val[1] = fma(vx.c[k].x, vy.c[k].x, fma(vx.c[k].y, vy.c[k].y, val[1]));
-      val[2] = fma(vx.c[k].x, vy.c[k].y, fma(-vx.c[k].y, vy.c[k].x, val[2]));
+      const double xx = vx.c[k].x, xy = vx.c[k].y, yx = vy.c[k].x, yy = vy.c[k].y;
+      val[0] = fma(xx, xx, fma(xy, xy, val[0]));
+      val[1] = fma(xx, yx, fma(xy, yy, val[1]));
+      val[2] = fma(xx, yy, fma(-xy, yx, val[2]));
     }
   }
   __shared__ double smem[3 * FS_BLOCK / 32];
   chunk_reduce<3>(val, smem, partial, nch);
+}
+
+// out (precision PO) = in (precision PI) over both parities
+template <int PI, int PO>
+__global__ void convert_full_kernel(Geom g, const char *in, size_t fbi, char *out, size_t fbo) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * g.vh) return;
+  const int half = i >= g.vh;
+  const int j = i - half * g.vh;
+  using RO = typename SpinorIO<PO>::R;
+  SpinorIO<PO>::store(out + half * fbo, g.stride, j,
+                      convert<RO>(SpinorIO<PI>::load(in + half * fbi, g.stride, j)));
+}
+
+// x64 += xs (FP32), xs = 0, over both parities
+__global__ void fold_kernel(Geom g, char *x64, size_t fb64, char *xs, size_t fb32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * g.vh) return;
+  const int half = i >= g.vh;
+  const int j = i - half * g.vh;
+  Vec3<double> x = SpinorIO<PREC_F64>::load(x64 + half * fb64, g.stride, j);
+  const Vec3<float> d = SpinorIO<PREC_F32>::load(xs + half * fb32, g.stride, j);
+  Vec3<float> z;
+  zero(z);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    x.c[k].x += (double)d.c[k].x;
+    x.c[k].y += (double)d.c[k].y;
+  }
+  SpinorIO<PREC_F64>::store(x64 + half * fb64, g.stride, j, x);
+  SpinorIO<PREC_F32>::store(xs + half * fb32, g.stride, j, z);
 }
 
 // out[v] = fixed-order sum of partial row v (one block per row)
@@ -199,20 +251,21 @@ struct FullOps {
   GaugeField *gf;
   cudaStream_t st;
   DslashConfig cfg;
+  int prec = PREC_F64;  // links and vectors of dslash, lincomb, mat, zaxpy, zdot
 
   int dslash(int out_parity, const char *in, char *out) {
     DslashArgs a;
     std::memset(&a, 0, sizeof(a));
     a.g = gf->g;
     a.out_parity = out_parity;
-    a.links = gf->link_ptr(PREC_F64, 18, out_parity);
-    a.ls = gf->scales(PREC_F64, 18);
+    a.links = gf->link_ptr(prec, 18, out_parity);
+    a.ls = gf->scales(prec, 18);
     a.in = in;
     a.out = out;
-    a.in_fb = a.out_fb = spinor_bytes(PREC_F64, gf->g.stride);
+    a.in_fb = a.out_fb = spinor_bytes(prec, gf->g.stride);
     a.nrhs = 1;
     a.gate = GATE_NONE;
-    if (launch_dslash(PREC_F64, 18, 1, MODE_PLAIN, PREC_F64, a, cfg.block, st)) return SQ_ERR_ARG;
+    if (launch_dslash(prec, 18, 1, MODE_PLAIN, prec, a, cfg.block, st)) return SQ_ERR_ARG;
     ctx->launches++;
     SQ_CUDA_TRY(cudaGetLastError());
     return SQ_OK;
@@ -220,7 +273,10 @@ struct FullOps {
   int lincomb(double a, const char *x, double b, const char *y, double c, const char *z,
               char *out) {
     if (gf->g.vh <= 0) return SQ_OK;
-    lincomb_kernel<<<blocks(gf->g), FS_BLOCK, 0, st>>>(gf->g, a, x, b, y, c, z, out);
+    if (prec == PREC_F32)
+      lincomb_kernel<PREC_F32><<<blocks(gf->g), FS_BLOCK, 0, st>>>(gf->g, a, x, b, y, c, z, out);
+    else
+      lincomb_kernel<PREC_F64><<<blocks(gf->g), FS_BLOCK, 0, st>>>(gf->g, a, x, b, y, c, z, out);
     ctx->launches++;
     SQ_CUDA_TRY(cudaGetLastError());
     return SQ_OK;
@@ -242,7 +298,7 @@ struct FullOps {
     return SQ_OK;
   }
   // whole-lattice vectors (both halves, fb bytes apart)
-  size_t fb() const { return spinor_bytes(PREC_F64, gf->g.stride); }
+  size_t fb() const { return spinor_bytes(prec, gf->g.stride); }
   int nch2() const { return (2 * gf->g.vh + CHUNK - 1) / CHUNK; }
   unsigned blocks2() const { return (unsigned)((2 * gf->g.vh + FS_BLOCK - 1) / FS_BLOCK); }
   // out = (m + D) in
@@ -257,8 +313,12 @@ struct FullOps {
   // out = x + a y + b z; with sums: sums[0] = |out|^2, sums[1..2] = <w, out>
   int zaxpy(const char *x, double2 a, const char *y, double2 b, const char *z, char *out,
             const char *w, double *partial, double *sums) {
-    zaxpy_kernel<<<blocks2(), FS_BLOCK, 0, st>>>(gf->g, fb(), x, a, y, b, z, out, w,
-                                                 sums ? partial : nullptr, nch2());
+    if (prec == PREC_F32)
+      zaxpy_kernel<PREC_F32><<<blocks2(), FS_BLOCK, 0, st>>>(gf->g, fb(), x, a, y, b, z, out, w,
+                                                             sums ? partial : nullptr, nch2());
+    else
+      zaxpy_kernel<PREC_F64><<<blocks2(), FS_BLOCK, 0, st>>>(gf->g, fb(), x, a, y, b, z, out, w,
+                                                             sums ? partial : nullptr, nch2());
     ctx->launches++;
     if (sums) {
       sum_rows_kernel<<<3, 128, 0, st>>>(partial, nch2(), sums);
@@ -269,7 +329,10 @@ struct FullOps {
   }
   // sums[0] = |x|^2, sums[1..2] = <x, y>
   int zdot(const char *x, const char *y, double *partial, double *sums) {
-    zdot_kernel<<<blocks2(), FS_BLOCK, 0, st>>>(gf->g, fb(), x, y, partial, nch2());
+    if (prec == PREC_F32)
+      zdot_kernel<PREC_F32><<<blocks2(), FS_BLOCK, 0, st>>>(gf->g, fb(), x, y, partial, nch2());
+    else
+      zdot_kernel<PREC_F64><<<blocks2(), FS_BLOCK, 0, st>>>(gf->g, fb(), x, y, partial, nch2());
     sum_rows_kernel<<<3, 128, 0, st>>>(partial, nch2(), sums);
     ctx->launches += 2;
     SQ_CUDA_TRY(cudaGetLastError());
@@ -450,6 +513,188 @@ extern "C" int cg_solve_full(sq_ctx *ctx, int gauge_id, const double *src, doubl
   return status;
 }
 
+namespace sq {
+namespace {
+
+// BiCGstab with FP32 vectors and Dslash and FP64 reliable updates (in the
+// manner of Sleijpen and van der Vorst's reliable-update scheme): the
+// solution increment xs accumulates in FP32 and is folded into the FP64
+// solution whenever |r| falls below delta times its maximum since the last
+// update, or the recursion claims convergence; r is then replaced by the
+// FP64 residual b - M x, and rho by <r^, r>, and the iteration continues.
+// A breakdown restarts from the FP64 residual with a new shadow residual.
+int bicgstab_mixed(sq_ctx *ctx, GaugeField *gf, cudaStream_t st, const double *src, double mass,
+                   double tol, const sq_cg_opts &o, bool dev, bool guess, double *x,
+                   sq_cg_stats *stats, std::chrono::steady_clock::time_point t0) {
+  using cplx = std::complex<double>;
+  const Geom &g = gf->g;
+  const size_t vol = (size_t)2 * g.vh, full_bytes = vol * 3 * 16;
+  FullOps o64{ctx, gf, st, tuned_dslash(ctx, *gf, PREC_F64, 18, 1, MODE_PLAIN, st), PREC_F64};
+  FullOps o32{ctx, gf, st, tuned_dslash(ctx, *gf, PREC_F32, 18, 1, MODE_PLAIN, st), PREC_F32};
+  const size_t fv64 = 2 * o64.fb(), fv32 = 2 * o32.fb();
+  const int nch = o64.nch2();
+  FullWork w;
+  w.ctx = ctx;
+  w.bytes = 4 * fv64 + 7 * fv32 + (dev ? 0 : full_bytes) + ((size_t)3 * nch + 8) * sizeof(double);
+  int rc = ctx->alloc(w.bytes, &w.base);
+  if (rc) return rc;
+  char *q = static_cast<char *>(w.base);
+  char *b64 = q, *x64 = b64 + fv64, *r64 = x64 + fv64, *t64 = r64 + fv64;
+  char *r = t64 + fv64, *rh = r + fv32, *p = rh + fv32, *v = p + fv32, *sv = v + fv32,
+       *t = sv + fv32, *xs = t + fv32;
+  char *after = xs + fv32;
+  double *stage = dev ? nullptr : reinterpret_cast<double *>(after);
+  double *partial = reinterpret_cast<double *>(after + (dev ? 0 : full_bytes));
+  double *sums = partial + (size_t)3 * nch;
+  const double2 zero = make_double2(0.0, 0.0);
+  auto z2 = [](cplx c) { return make_double2(c.real(), c.imag()); };
+  double h[6];
+  auto fetch = [&](int n) -> int {
+    SQ_CUDA_TRY(cudaMemcpyAsync(h, sums, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SQ_CUDA_TRY(cudaStreamSynchronize(st));
+    return SQ_OK;
+  };
+  const unsigned blocks2 = o64.blocks2();
+
+  const double *bsrc = src;
+  if (!dev) {
+    SQ_CUDA_TRY(cudaMemcpyAsync(stage, src, full_bytes, cudaMemcpyHostToDevice, st));
+    bsrc = stage;
+  }
+  if ((rc = o64.split(bsrc, b64, b64 + fv64 / 2))) return rc;
+  if (guess) {
+    const double *gsrc = x;
+    if (!dev) {
+      SQ_CUDA_TRY(cudaMemcpyAsync(stage, x, full_bytes, cudaMemcpyHostToDevice, st));
+      gsrc = stage;
+    }
+    if ((rc = o64.split(gsrc, x64, x64 + fv64 / 2))) return rc;
+  } else {
+    SQ_CUDA_TRY(cudaMemsetAsync(x64, 0, fv64, st));
+  }
+  SQ_CUDA_TRY(cudaMemsetAsync(xs, 0, fv32, st));
+  if ((rc = o64.zdot(b64, b64, partial, sums)) || (rc = fetch(1))) return rc;
+  const double bn2 = h[0];
+  if (!std::isfinite(bn2)) return SQ_ERR_NONFINITE;
+  const double stop2 = tol * tol * bn2;
+  const double delta = o.delta >= 0 ? o.delta : 0.1;
+
+  // x64 += xs, xs = 0; r64 = b - M x64; r = r64 (FP32): returns |r64|^2 in *rr
+  int nres = 0;
+  auto reliable = [&](double *rr) -> int {
+    ++nres;
+    fold_kernel<<<blocks2, FS_BLOCK, 0, st>>>(g, x64, fv64 / 2, xs, fv32 / 2);
+    ctx->launches++;
+    SQ_CUDA_TRY(cudaGetLastError());
+    int e;
+    if ((e = o64.mat(mass, x64, t64))) return e;
+    if ((e = o64.zaxpy(b64, make_double2(-1.0, 0.0), t64, zero, nullptr, r64, nullptr, partial,
+                       sums)) ||
+        (e = fetch(1)))
+      return e;
+    convert_full_kernel<PREC_F64, PREC_F32><<<blocks2, FS_BLOCK, 0, st>>>(g, r64, fv64 / 2, r,
+                                                                          fv32 / 2);
+    ctx->launches++;
+    SQ_CUDA_TRY(cudaGetLastError());
+    *rr = h[0];
+    return std::isfinite(h[0]) ? SQ_OK : SQ_ERR_NONFINITE;
+  };
+
+  int it = 0, status = SQ_NOT_CONVERGED;
+  double rr = 0.0;
+  if (bn2 == 0) {
+    SQ_CUDA_TRY(cudaMemsetAsync(x64, 0, fv64, st));
+    status = SQ_OK;
+  }
+  for (int restart = 0; bn2 > 0 && restart < 64; ++restart) {
+    if ((rc = reliable(&rr))) return rc;
+    if (rr <= stop2) {
+      status = SQ_OK;
+      break;
+    }
+    if (it >= o.max_iter) break;
+    // a new shadow residual
+    SQ_CUDA_TRY(cudaMemcpyAsync(rh, r, fv32, cudaMemcpyDeviceToDevice, st));
+    SQ_CUDA_TRY(cudaMemsetAsync(p, 0, fv32, st));
+    SQ_CUDA_TRY(cudaMemsetAsync(v, 0, fv32, st));
+    if ((rc = o32.zdot(rh, r, partial, sums)) || (rc = fetch(3))) return rc;
+    cplx rho_old(1.0, 0.0), alpha(1.0, 0.0), omega(1.0, 0.0), rho(h[1], h[2]);
+    double maxr = std::sqrt(rr);
+    bool done = false;
+    while (it < o.max_iter) {
+      if (rho == cplx(0.0, 0.0)) break;
+      const cplx beta = (rho / rho_old) * (alpha / omega);
+      if ((rc = o32.zaxpy(r, z2(beta), p, z2(-beta * omega), v, p, nullptr, nullptr, nullptr)))
+        return rc;
+      if ((rc = o32.mat(mass, p, v))) return rc;
+      if ((rc = o32.zdot(rh, v, partial, sums)) || (rc = fetch(3))) return rc;
+      const cplx d(h[1], h[2]);
+      if (d == cplx(0.0, 0.0)) break;
+      alpha = rho / d;
+      if ((rc = o32.zaxpy(r, z2(-alpha), v, zero, nullptr, sv, nullptr, partial, sums + 3)))
+        return rc;
+      if ((rc = o32.mat(mass, sv, t))) return rc;
+      if ((rc = o32.zdot(t, sv, partial, sums)) || (rc = fetch(6))) return rc;
+      ++it;
+      const double ss = h[3], tt = h[0];
+      const cplx ts(h[1], h[2]);
+      if (!std::isfinite(ss) || !std::isfinite(tt)) return SQ_ERR_NONFINITE;
+      if (ss <= stop2 || tt == 0.0) {  // x += alpha p finishes it (checked in FP64)
+        if ((rc = o32.zaxpy(xs, z2(alpha), p, zero, nullptr, xs, nullptr, nullptr, nullptr)))
+          return rc;
+        break;
+      }
+      omega = ts / tt;
+      if ((rc = o32.zaxpy(xs, z2(alpha), p, z2(omega), sv, xs, nullptr, nullptr, nullptr)))
+        return rc;
+      if ((rc = o32.zaxpy(sv, z2(-omega), t, zero, nullptr, r, rh, partial, sums)) ||
+          (rc = fetch(3)))
+        return rc;
+      rho_old = rho;
+      rho = cplx(h[1], h[2]);
+      const double rn2 = h[0];
+      if (omega == cplx(0.0, 0.0)) break;
+      if (rn2 <= stop2 || std::sqrt(rn2) < delta * maxr) {
+        if ((rc = reliable(&rr))) return rc;
+        if (rr <= stop2) {
+          done = true;
+          status = SQ_OK;
+          break;
+        }
+        if ((rc = o32.zdot(rh, r, partial, sums)) || (rc = fetch(3))) return rc;
+        rho = cplx(h[1], h[2]);
+        maxr = std::sqrt(rr);
+      } else {
+        maxr = std::max(maxr, std::sqrt(rn2));
+      }
+    }
+    if (done) break;
+  }
+  // a final fold and FP64 residual unless the last step just made one
+  if (status != SQ_OK && bn2 > 0 && (rc = reliable(&rr))) return rc;
+  if (bn2 > 0 && rr <= stop2) status = SQ_OK;
+  double *xdst = dev ? x : stage;
+  if ((rc = o64.merge(x64, x64 + fv64 / 2, xdst))) return rc;
+  if (!dev) SQ_CUDA_TRY(cudaMemcpyAsync(x, stage, full_bytes, cudaMemcpyDeviceToHost, st));
+  SQ_CUDA_TRY(cudaStreamSynchronize(st));
+  if (stats) {
+    const double secs =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    std::memset(stats, 0, sizeof(*stats));
+    stats->status = status;
+    stats->iterations = it;
+    stats->reliable_updates = nres;
+    stats->true_residual = bn2 > 0 ? std::sqrt(rr / bn2) : 0.0;
+    stats->seconds = secs;
+    stats->gflops =
+        (secs > 0) ? (4.0 * 1146.0 * g.vh + 100.0 * 2 * g.vh) * it / secs * 1e-9 : 0.0;
+  }
+  return status;
+}
+
+}  // namespace
+}  // namespace sq
+
 // BiCGstab (van der Vorst, SIAM J. Sci. Stat. Comput. 13 (1992) 631) on the
 // whole-lattice matrix M = m + D itself -- the BiCG-family inverter of the
 // paper's list (Sec. 3) -- in FP64.  The recurrences run on the host from
@@ -462,12 +707,14 @@ extern "C" int bicgstab_solve_full(sq_ctx *ctx, int gauge_id, const double *src,
   if (!std::isfinite(mass) || !(tol > 0) || !std::isfinite(tol)) return SQ_ERR_ARG;
   sq_cg_opts o;
   sq_cg_opts_default(&o);
+  o.precision = PREC_F64;  // without options: FP64
   if (opts_in) o = *opts_in;
   if (o.max_iter <= 0) return SQ_ERR_ARG;
+  if (o.precision != PREC_F64 && o.precision != PREC_F32) return SQ_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> solve_lock(ctx->solve_mu);
   GaugeField *gf = ctx->gauge(gauge_id);
   if (!gf) return SQ_ERR_NOTFOUND;
-  if (!gf->has(PREC_F64, 18)) return SQ_ERR_UNSUPPORTED;
+  if (!gf->has(PREC_F64, 18) || !gf->has(o.precision, 18)) return SQ_ERR_UNSUPPORTED;
   const Geom &g = gf->g;
   const bool dev = (o.flags & SQ_CG_DEVICE_PTRS) != 0;
   const bool guess = (o.flags & SQ_CG_INITIAL_GUESS) != 0;
@@ -481,6 +728,8 @@ extern "C" int bicgstab_solve_full(sq_ctx *ctx, int gauge_id, const double *src,
   if (st == ctx->stream)  // a default stream (NULL: the legacy one): its work first
     SQ_CUDA_TRY(cudaStreamSynchronize(o.stream ? (cudaStream_t)o.stream : cudaStreamLegacy));
 
+  if (o.precision == PREC_F32)
+    return bicgstab_mixed(ctx, gf, st, src, mass, tol, o, dev, guess, x, stats, t0);
   FullOps ops{ctx, gf, st, tuned_dslash(ctx, *gf, PREC_F64, 18, 1, MODE_PLAIN, st)};
   const size_t fv = 2 * ops.fb();  // one whole-lattice vector
   const int nch = ops.nch2();

@@ -409,10 +409,12 @@ class Context:
             _check(status, 'cg_solve_full')
         return x, st.as_dict()
 
-    def bicgstab_solve_full(self, gauge_id, src, mass, tol, max_iter=100000, x0=None,
-                            stream=None, check=True):
-        """Solve (m + D) x = src on the whole lattice by FP64 BiCGstab on M
-        itself.  Arrays as cg_solve_full.  Returns (x, stats dict)."""
+    def bicgstab_solve_full(self, gauge_id, src, mass, tol, precision='f64', delta=-1.0,
+                            max_iter=100000, x0=None, stream=None, check=True):
+        """Solve (m + D) x = src on the whole lattice by BiCGstab on M itself:
+        precision 'f64', or 'f32' (FP32 vectors and Dslash with FP64 reliable
+        updates at |r| < delta max|r|, default delta 0.1).  Arrays as
+        cg_solve_full.  Returns (x, stats dict)."""
         dev = _is_device(src)
         if dev:
             s = src.contiguous()
@@ -427,7 +429,7 @@ class Context:
                 x.copy_(x0)
             else:
                 x[...] = np.asarray(x0)
-        o = self._opts('f64', 18, -1.0, max_iter, 16, flags, stream)
+        o = self._opts(precision, 18, delta, max_iter, 16, flags, stream)
         st = CgStats()
         status = self._lib.bicgstab_solve_full(self.handle, gauge_id, _ptr(s), float(mass),
                                                float(tol), ctypes.byref(o), _ptr(x),

@@ -80,6 +80,24 @@ def test_bicgstab_special_cases(sq):
         sq.gauge_free(gid)
 
 
+@pytest.mark.parametrize('dims,mass', [((4, 4, 4, 4), 0.05), ((4, 6, 8, 10), 0.1)])
+def test_bicgstab_mixed_precision_matches_oracle(sq, dims, mass):
+    """FP32 vectors and Dslash with FP64 reliable updates: the same acceptance
+    against the oracle's FP64 BiCGstab solution."""
+    fat, lng = gauge(dims, 0.3, 0)
+    b = _src(dims, 3)
+    tol = 1e-10
+    gid = sq.gauge_load(dims, fat, lng)
+    try:
+        x, st = sq.bicgstab_solve_full(gid, b, mass, tol, precision='f32')
+        assert st['status'] == 0 and st['reliable_updates'] >= 2
+        x_ref, _, _ = oracle.bicgstab_full(dims, fat, lng, mass, b, tol)
+        r = _check(dims, fat, lng, mass, b, x, tol, x_ref)
+        assert abs(st['true_residual'] - r) <= 1e-3 * r
+    finally:
+        sq.gauge_free(gid)
+
+
 def test_bicgstab_full_size_20x64(sq):
     """The benchmark lattice 20^3 x 64 (eps 0.25), am 0.05, tol 1e-8."""
     from paper_1411_2223_gb300 import sq as sqm
@@ -88,9 +106,10 @@ def test_bicgstab_full_size_20x64(sq):
     b = _src(dims, 0)
     gid = sq.gauge_load(dims, fat, lng, flags=sqm.GAUGE_NO_I16 | sqm.GAUGE_NO_LONG12)
     try:
-        x, st = sq.bicgstab_solve_full(gid, b, 0.05, 1e-8)
-        assert st['status'] == 0
-        r = _check(dims, fat, lng, 0.05, b, x, 1e-8)
-        assert abs(st['true_residual'] - r) <= 1e-4 * r
+        for prec in ('f64', 'f32'):
+            x, st = sq.bicgstab_solve_full(gid, b, 0.05, 1e-8, precision=prec)
+            assert st['status'] == 0
+            r = _check(dims, fat, lng, 0.05, b, x, 1e-8)
+            assert abs(st['true_residual'] - r) <= 1e-4 * r
     finally:
         sq.gauge_free(gid)
