@@ -183,8 +183,9 @@ int gauge_fatten(sq_ctx *ctx, const int dims[4], const double *thin_dev, double 
 int gauge_fatten_asqtad(sq_ctx *ctx, const int dims[4], const double *thin_dev,
                         const double coeffs[6], double *fat_dev, double *lng_dev, void *stream);
 
-/* gauge_fatten followed by gauge_load: thin links in (host pointer, or device
- * with SQ_GAUGE_DEVICE_PTRS), a gauge id out.  The fat and long links exist
+/* gauge_fatten followed by gauge_load (the smeared links of the paper's MILC
+ * lattices, Sec. 2, built here from thin links): thin links in (host
+ * pointer, or device with SQ_GAUGE_DEVICE_PTRS), a gauge id out.  The fat and long links exist
  * on the device only transiently (staging outside the HBM budget, freed on
  * return).  Other flags as for gauge_load. */
 int gauge_load_thin(sq_ctx *ctx, const int dims[4], const double *thin, double c1, double c3,
@@ -256,11 +257,13 @@ int npr_four_fermion(sq_ctx *ctx, const int dims[4], const double *links_dev,
                      double *out_dev, double *out_hc_dev, void *stream);
 
 /* Bytes of one packed parity-half vector of `prec` for this gauge field's
- * lattice, and the plane stride in sites. */
+ * lattice, and the plane stride in sites (the device layout of this library;
+ * the paper prints none). */
 int sq_spinor_bytes(sq_ctx *ctx, int gauge_id, int prec, size_t *bytes, int *stride);
 
-/* Canonical (complex128) <-> packed device vector of one parity.  Both
- * pointers are device pointers; asynchronous on `stream`. */
+/* Canonical (complex128) <-> packed device vector of one parity (this
+ * library's layout; the paper prints none).  Both pointers are device
+ * pointers; asynchronous on `stream`. */
 int sq_pack_spinor(sq_ctx *ctx, int gauge_id, int prec, const double *canon_dev,
                    void *packed_dev, void *stream);
 int sq_unpack_spinor(sq_ctx *ctx, int gauge_id, int prec, const void *packed_dev,
@@ -269,14 +272,16 @@ int sq_unpack_spinor(sq_ctx *ctx, int gauge_id, int prec, const void *packed_dev
 /* ---- operators ------------------------------------------------------------ */
 
 /* out = D_{p,1-p} in: the asqtad Dslash from parity 1-out_parity to parity
- * out_parity (the 16 SU(3) mat-vecs per site above), in `prec` with long
+ * out_parity (the 16 SU(3) mat-vecs per site above; the operator in which the
+ * paper's CG inverter spends its time, Sec. 2, Fig. 1), in `prec` with long
  * links in `long_recon` (18 or 12) form.  in/out are packed device vectors
  * (distinct buffers).  Asynchronous on `stream`; no host synchronisation. */
 int dslash_apply(sq_ctx *ctx, int gauge_id, int out_parity, int prec, int long_recon,
                  const void *in_dev, void *out_dev, void *stream);
 
-/* out = (m^2 - D_eo D_oe) in on the even parity: the CG operator, as the two
- * Dslash kernels the solver runs (the second with the m^2 epilogue).  Uses a
+/* out = (m^2 - D_eo D_oe) in on the even parity: the operator of the paper's
+ * even-odd CG inverter (Sec. 2), as two Dslash kernels (the second with the
+ * m^2 epilogue).  Uses a
  * context-owned odd-parity temporary. */
 int mdagm_apply(sq_ctx *ctx, int gauge_id, int prec, int long_recon, double mass,
                 const void *in_dev, void *out_dev, void *stream);
@@ -315,7 +320,9 @@ int cg_solve(sq_ctx *ctx, int gauge_id, const double *src_even, double mass, dou
              const sq_cg_opts *opts, double *x_even, sq_cg_stats *stats);
 
 /* Batched solve of nrhs systems (m_j^2 - D_eo D_oe) x_j = b_j on one gauge
- * field: every Dslash streams each link once for all right-hand sides.
+ * field, each by the CG of cg_solve (the paper's inverter, Sec. 2, solves one
+ * system at a time; batching is this library's): every Dslash streams each
+ * link once for all right-hand sides.
  * src/x: nrhs canonical vectors back to back; masses: nrhs values; stats:
  * nrhs entries (may be NULL).  Each system follows cg_solve's algorithm and
  * stops on its own. */
@@ -323,8 +330,9 @@ int cg_solve_multi(sq_ctx *ctx, int gauge_id, int nrhs, const double *src,
                    const double *masses, double tol, const sq_cg_opts *opts,
                    double *x, sq_cg_stats *stats);
 
-/* Multi-shift CG: (m_i^2 - D_eo D_oe) x_i = b for nshift masses from one
- * Krylov space (Jegerlehner's shifted recurrences), run in the sloppy
+/* Multi-shift CG (not in the paper; the masses of Sec. 2's inverter solved
+ * together): (m_i^2 - D_eo D_oe) x_i = b for nshift masses from one Krylov
+ * space (Jegerlehner's shifted recurrences, hep-lat/9612014), run in the sloppy
  * precision to max(tol, 1e-5 for FP32 / 1e-3 for 16-bit), then refined per
  * shift by the batched mixed-precision CG above started from the shifted
  * solutions.  x: nshift canonical vectors; stats: nshift entries (may be NULL). */
@@ -350,8 +358,8 @@ int cg_solve_multishift(sq_ctx *ctx, int gauge_id, const double *src, int nshift
 int cg_solve_full(sq_ctx *ctx, int gauge_id, const double *src, double mass, double tol,
                   const sq_cg_opts *opts, double *x, sq_cg_stats *stats);
 
-/* out = (m + D) in on the whole lattice, in FP64: the staggered operator
- * without even-odd preconditioning.  in_dev/out_dev: distinct device
+/* out = (m + D) in on the whole lattice, in FP64: the staggered matrix of the
+ * paper's inverter (Sec. 2) without even-odd preconditioning.  in_dev/out_dev: distinct device
  * full-lattice vectors [site_lex][colour] complex128.  Uses device scratch
  * for the call (HBM budget) and returns once out is written. */
 int dirac_apply(sq_ctx *ctx, int gauge_id, double mass, const double *in_dev, double *out_dev,
@@ -359,8 +367,9 @@ int dirac_apply(sq_ctx *ctx, int gauge_id, double mass, const double *in_dev, do
 
 /* ---- serving -------------------------------------------------------------- */
 
-/* Continuous-batching request loop.  serve_submit copies the host source and
- * queues one solve; a scheduler thread admits queued requests into free slots
+/* Continuous-batching request loop (not in the paper: a serving interface of
+ * this library around the solves of Sec. 2).  serve_submit copies the host
+ * source and queues one solve; a scheduler thread admits queued requests into free slots
  * of the running batched CG of their gauge field (at iteration-block
  * boundaries) while the HBM budget allows, runs the batches of all gauge
  * fields concurrently on separate streams and retires converged slots.
