@@ -10,7 +10,6 @@ import numpy as np
 import pytest
 
 import oracle
-import synth
 from gpu_helpers import gauge, rel, to_dev
 
 pytestmark = pytest.mark.gpu

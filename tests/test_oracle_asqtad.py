@@ -10,7 +10,6 @@
 * gauge covariance under random SU(3);
 * the Naik link over c_N is SU(3).
 """
-import itertools
 
 import numpy as np
 import pytest

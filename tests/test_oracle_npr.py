@@ -27,7 +27,6 @@ The contraction against:
 import itertools
 
 import numpy as np
-import pytest
 
 import oracle
 import synth
