@@ -501,6 +501,64 @@ def npr_cpu_baseline(inputs, n_hc=4096):
                       % (n_hc, nhc, len(ops), dt)}
 
 
+def fp64_error(x, x64):
+    """|x - x64| / |x64| (device tensors)."""
+    import torch
+    return float(torch.linalg.vector_norm(x - x64) / torch.linalg.vector_norm(x64))
+
+
+def batched_dslash(ctx, sq, dims, stream, nrhs=BATCH_NRHS):
+    """The FP32 18-real Dslash on 12 right-hand sides in one launch
+    (dslash_apply_multi) at the tuner's tile, and the CG's two batched
+    kernels (sq_time_dslash): device time per launch against the HBM
+    roofline, links counted once per launch plus every system's own
+    vectors."""
+    import numpy as np
+    import torch
+    import synth
+    vh = int(np.prod(dims)) // 2
+    gid = None
+    fat, lng = synth.gauge_field(dims, EPS, GAUGE_SEED)
+    gid = ctx.gauge_load(dims, fat, lng, flags=sq.GAUGE_NO_I16 | sq.GAUGE_NO_LONG12 |
+                         sq.GAUGE_NO_F64)
+    del fat, lng
+    nbytes, _ = ctx.spinor_bytes(gid, 'f32')
+    a = torch.zeros(nrhs * nbytes, dtype=torch.uint8, device='cuda')
+    c = torch.zeros_like(a)
+    src = torch.from_numpy(synth.gaussian_source(vh, SRC_SEED)).cuda()
+    for j in range(nrhs):
+        ctx.pack_spinor(gid, 'f32', src, a[j * nbytes:(j + 1) * nbytes], stream)
+    iters = 40
+    for k in range(4):
+        ctx.dslash_apply_multi(gid, k & 1, 'f32', 18, nrhs, a if k & 1 else c,
+                               c if k & 1 else a, stream)
+    ms, _ = timed(lambda: [ctx.dslash_apply_multi(gid, k & 1, 'f32', 18, nrhs, a if k & 1 else c,
+                                                  c if k & 1 else a, stream)
+                           for k in range(iters)], stream)
+    us = ms * 1e3 / iters
+    links = 1152
+    peak, kind = measured_peak()
+    out = {'plain': {'us': round(us, 2), 'rhs_tile': ctx.tuned_launch(gid, 'f32', 18, nrhs,
+                                                                       'plain')[1],
+                     'algorithmic_bytes_per_site': links + nrhs * 48,
+                     'GBs': round((links + nrhs * 48) * vh / (us * 1e-6) / 1e9, 1)}}
+    # the CG's kernels: D_oe with <p, A p> reads p and writes t per system
+    # (plus own p), D_eo with the update reads t, p, r, xs and writes r, xs
+    for mode, per_sys in (('cg_oe', 72), ('cg_eo', 144)):
+        us_m = ctx.time_dslash(gid, 'f32', 18, nrhs, mode, 50, stream)
+        b = links + nrhs * per_sys
+        out[mode] = {'us': round(us_m, 2),
+                     'rhs_tile': ctx.tuned_launch(gid, 'f32', 18, nrhs, mode)[1],
+                     'algorithmic_bytes_per_site': b,
+                     'GBs': round(b * vh / (us_m * 1e-6) / 1e9, 1)}
+    for v in out.values():
+        v['frac_of_hbm'] = round(v['GBs'] / peak, 4)
+    out['peak_GBs'] = peak
+    out['peak_kind'] = kind
+    ctx.gauge_free(gid)
+    return out
+
+
 def batched_workload(ctx, sq, stream):
     """24^3 x 64: 12 right-hand sides in one batched solve against 12 single
     solves, and 8 masses in one multi-shift solve against 8 single solves."""
@@ -528,11 +586,20 @@ def batched_workload(ctx, sq, stream):
         return ctx.cg_solve_multishift(gid, srcs[0], shifts, TOL, stream=stream)[1]
     multi()
     ms_multi, st_multi = timed(multi, stream)
+    x_multi = xs.clone()
     singles(srcs[:1], masses[:1])
     ms_single, st_single = timed(lambda: singles(srcs, masses), stream)
     mshift()
     ms_shift, st_shift = timed(mshift, stream)
+    x_shift = ctx.cg_solve_multishift(gid, srcs[0], shifts, TOL, stream=stream)[0]
     ms_shift_single, _ = timed(lambda: singles([srcs[0]] * len(shifts), shifts), stream)
+    # FP64 error of every result against the plain FP64 GPU CG of the same
+    # system (batched FP64 solves, to 1e-10)
+    ref = ctx.cg_solve_multi(gid, srcs, masses, 1e-10, precision='f64', stream=stream)[0]
+    err_multi = [fp64_error(x_multi[j], ref[j]) for j in range(BATCH_NRHS)]
+    ref = ctx.cg_solve_multi(gid, srcs[0].expand(len(shifts), -1, -1).contiguous(), shifts,
+                             1e-10, precision='f64', stream=stream)[0]
+    err_shift = [fp64_error(x_shift[j], ref[j]) for j in range(len(shifts))]
     ctx.gauge_free(gid)
     worst = max(s['true_residual'] for s in st_multi + st_shift)
     return {'workload': '24^3x64 (eps 0.25 synthetic links, seed 0), tol 1e-8, FP32 + FP64 '
@@ -542,11 +609,15 @@ def batched_workload(ctx, sq, stream):
                           'ms_per_solve': round(ms_multi / BATCH_NRHS, 3),
                           'single_solves_ms': round(ms_single, 3),
                           'speedup_vs_single': round(ms_single / ms_multi, 3),
-                          'iterations_max': max(s['iterations'] for s in st_multi)},
+                          'iterations_max': max(s['iterations'] for s in st_multi),
+                          'rhs_tile': [st_multi[0]['oe_rhs_tile'], st_multi[0]['eo_rhs_tile']],
+                          'fp64_error_vs_fp64_cg': err_multi},
             'multi_shift': {'shifts': len(shifts), 'ms': round(ms_shift, 3),
                             'single_solves_ms': round(ms_shift_single, 3),
                             'speedup_vs_single': round(ms_shift_single / ms_shift, 3),
-                            'iterations': [s['iterations'] for s in st_shift]},
+                            'iterations': [s['iterations'] for s in st_shift],
+                            'fp64_error_vs_fp64_cg': err_shift},
+            'dslash_12rhs': batched_dslash(ctx, sq, dims, stream),
             'worst_true_residual': worst}
 
 

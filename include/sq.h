@@ -40,10 +40,11 @@
  * streams   `void *stream` is a cudaStream_t.  The blocking calls (solves,
  *           dirac_apply) run on it, or on the context's stream when it is
  *           NULL or a default stream, after waiting for that stream's work.
- *           The asynchronous operator calls (dslash_apply, mdagm_apply, the
- *           pack helpers) run on the context's stream for NULL; the newer
- *           ones (gauge_fatten*, npr_four_fermion) on the legacy default
- *           stream for NULL, as CUDA does.
+ *           The asynchronous calls (dslash_apply, dslash_apply_multi,
+ *           mdagm_apply, mdagm_apply_static, the pack helpers,
+ *           gauge_fatten*, npr_four_fermion) run on `stream` as given: NULL
+ *           is the legacy default stream, as in CUDA, so they are ordered
+ *           with all other work on it (torch's default stream included).
  * errors    every call returns an sq_status; nothing aborts or throws.
  *           Non-finite inputs give SQ_ERR_NONFINITE.
  * ownership the caller owns every pointer it passes; calls that take host
@@ -112,6 +113,11 @@ typedef struct {
     double true_residual;  /* |b - A x| / |b|, FP64, computed on the GPU       */
     double seconds;        /* wall time of the solve (host clock)              */
     double gflops;         /* 2364 flop per even site per iteration            */
+    /* Launch shapes of the CG's two sloppy Dslash kernels as launched (the
+     * tuner's choice, or a SQ_TUNE_CACHE entry): threads per block and
+     * right-hand sides per thread of the D_oe kernel (with the reduction)
+     * and of the D_eo kernel (with the update).  0 where no batched CG ran. */
+    int oe_block, oe_rhs_tile, eo_block, eo_rhs_tile;
 } sq_cg_stats;
 
 typedef struct {
@@ -279,6 +285,38 @@ int sq_unpack_spinor(sq_ctx *ctx, int gauge_id, int prec, const void *packed_dev
 int dslash_apply(sq_ctx *ctx, int gauge_id, int out_parity, int prec, int long_recon,
                  const void *in_dev, void *out_dev, void *stream);
 
+/* out_j = D_{p,1-p} in_j for nrhs right-hand sides in one launch (1 <= nrhs
+ * <= 64): the Dslash of dslash_apply, with each link read once for a tile of
+ * right-hand sides per thread (the batched form of the operator the paper's
+ * CG spends its time in, Sec. 2; batching is this library's).  in/out:
+ * nrhs packed vectors back to back, each sq_spinor_bytes long, in distinct
+ * buffers.  The tile and block size are the tuner's (sq_tuned_launch, mode
+ * 0).  Asynchronous on `stream`. */
+int dslash_apply_multi(sq_ctx *ctx, int gauge_id, int out_parity, int prec, int long_recon,
+                       int nrhs, const void *in_dev, void *out_dev, void *stream);
+
+/* The launch shape the library uses for one of its Dslash kernels on this
+ * gauge field: threads per block and right-hand sides per thread, for `nrhs`
+ * systems in `prec` with `long_recon`-real long links.  mode: 0 the plain
+ * Dslash (dslash_apply, dslash_apply_multi, the FP64 reliable-update pair),
+ * 1 with the m^2 epilogue (mdagm_apply, multi-shift), 3 the CG's D_oe kernel
+ * with its reduction, 4 the CG's D_eo kernel with its update.  The shape is
+ * chosen by timing the candidates on first use (which allocates scratch and
+ * synchronises `stream`) unless SQ_TUNE_CACHE or an earlier call fixed it.
+ * (The paper's QUDA path tunes its launches at run time, Sec. 3.) */
+int sq_tuned_launch(sq_ctx *ctx, int gauge_id, int prec, int long_recon, int nrhs, int mode,
+                    void *stream, int *block, int *rhs_tile);
+
+/* Device time of one of those Dslash kernels (modes as sq_tuned_launch) at
+ * the launch shape the library uses: `reps` back-to-back launches on
+ * synthetic vectors (the gauge field's own links, running systems for the
+ * reducing modes), timed with CUDA events on `stream` after a warm-up;
+ * *us_per_launch is the mean.  For rooflines of the kernels the solvers run
+ * inside CUDA graphs (the paper measures its CG in GFLOPS, Table 2).
+ * Allocates scratch for the call and synchronises `stream`. */
+int sq_time_dslash(sq_ctx *ctx, int gauge_id, int prec, int long_recon, int nrhs, int mode,
+                   int reps, void *stream, float *us_per_launch);
+
 /* out = (m^2 - D_eo D_oe) in on the even parity: the operator of the paper's
  * even-odd CG inverter (Sec. 2), as two Dslash kernels (the second with the
  * m^2 epilogue).  Uses a
@@ -286,21 +324,25 @@ int dslash_apply(sq_ctx *ctx, int gauge_id, int out_parity, int prec, int long_r
 int mdagm_apply(sq_ctx *ctx, int gauge_id, int prec, int long_recon, double mass,
                 const void *in_dev, void *out_dev, void *stream);
 
-/* Same operator as mdagm_apply, for callers that must not allocate device
- * memory at call time: work recorded into a CUDA graph by stream capture,
- * applications that reserve all of HBM through their own allocator or pool,
- * latency-critical loops that cannot take a first-use cudaMalloc.  (The paper
- * has no counterpart; this is an interface of this library only.)
+/* Same operator as mdagm_apply, for callers that cannot let the library
+ * allocate device memory when they call it: applications that reserve all of
+ * HBM up front through their own allocator or memory pool and forbid
+ * libraries to allocate behind it, and latency-critical loops in which a
+ * first-use cudaMalloc would be an unpredictable stall (mdagm_apply
+ * allocates its temporary on first use per gauge field and precision).  (The
+ * paper has no counterpart; this is an interface of this library only.)
  * The odd-parity temporary lives in one fixed device array of
  * SQ_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the
- * process exits; the call allocates nothing (no cudaMalloc, no tuning).
- * The packed vector of one parity (sq_spinor_bytes) must fit that array --
- * e.g. up to 524288 sites per parity in FP32 (a 20^3 x 64 lattice has
- * 256000) -- otherwise SQ_ERR_ARG.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the array and the temporary is fully
- * rewritten by each call, but calls that overlap on the GPU (other streams,
- * other threads) race on it: serialise them.  in/out as for mdagm_apply. */
+ * process exits; the call allocates nothing (no cudaMalloc, no cudaFree, no
+ * tuning).  The packed vector of one parity (sq_spinor_bytes) must fit that
+ * array -- e.g. up to 524288 sites per parity in FP32 (a 20^3 x 64 lattice
+ * has 256000) -- otherwise SQ_ERR_ARG.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) as a one-time set-up;
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents; the temporary is fully rewritten by
+ * each call before it is read, so nothing needs clearing, but calls that
+ * overlap on the GPU (other streams, other threads) race on it: serialise
+ * them.  in/out and stream as for mdagm_apply. */
 #define SQ_STATIC_SCRATCH_BYTES (12u << 20)
 int mdagm_apply_static(sq_ctx *ctx, int gauge_id, int prec, int long_recon, double mass,
                        const void *in_dev, void *out_dev, void *stream);

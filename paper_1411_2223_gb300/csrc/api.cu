@@ -1,4 +1,5 @@
 // The C ABI (include/sq.h): contexts, gauge fields, operators and solvers.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -411,6 +412,54 @@ extern "C" int dslash_apply(sq_ctx *ctx, int gauge_id, int out_parity, int prec,
   return SQ_OK;
 }
 
+extern "C" int dslash_apply_multi(sq_ctx *ctx, int gauge_id, int out_parity, int prec,
+                                  int long_recon, int nrhs, const void *in_dev, void *out_dev,
+                                  void *stream) {
+  if (!ctx || !in_dev || !out_dev || in_dev == out_dev) return SQ_ERR_ARG;
+  if (out_parity < 0 || out_parity > 1 || prec < 0 || prec > 2) return SQ_ERR_ARG;
+  if (long_recon != 18 && long_recon != 12) return SQ_ERR_ARG;
+  if (nrhs < 1 || nrhs > 64) return SQ_ERR_ARG;
+  GaugeField *gf = ctx->gauge(gauge_id);
+  if (!gf) return SQ_ERR_NOTFOUND;
+  if (!gf->has(prec, long_recon)) return SQ_ERR_UNSUPPORTED;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  DslashConfig cfg = tuned_dslash(ctx, *gf, prec, long_recon, nrhs, MODE_PLAIN, st);
+  DslashArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = gf->g;
+  a.out_parity = out_parity;
+  a.links = gf->link_ptr(prec, long_recon, out_parity);
+  a.ls = gf->scales(prec, long_recon);
+  a.in = static_cast<const char *>(in_dev);
+  a.out = static_cast<char *>(out_dev);
+  a.in_fb = a.out_fb = spinor_bytes(prec, gf->g.stride);
+  a.nrhs = nrhs;
+  a.gate = GATE_NONE;
+  if (launch_dslash(prec, long_recon, cfg.nr, MODE_PLAIN, prec, a, cfg.block, st))
+    return SQ_ERR_ARG;
+  ctx->launches++;
+  SQ_CUDA_TRY(cudaGetLastError());
+  return SQ_OK;
+}
+
+extern "C" int sq_tuned_launch(sq_ctx *ctx, int gauge_id, int prec, int long_recon, int nrhs,
+                               int mode, void *stream, int *block, int *rhs_tile) {
+  if (!ctx || !block || !rhs_tile || prec < 0 || prec > 2) return SQ_ERR_ARG;
+  if (long_recon != 18 && long_recon != 12) return SQ_ERR_ARG;
+  if (nrhs < 1 || nrhs > 64) return SQ_ERR_ARG;
+  if (mode != MODE_PLAIN && mode != MODE_MDAGM && mode != MODE_NORM && mode != MODE_UPDATE)
+    return SQ_ERR_ARG;
+  GaugeField *gf = ctx->gauge(gauge_id);
+  if (!gf) return SQ_ERR_NOTFOUND;
+  if (!gf->has(prec, long_recon)) return SQ_ERR_UNSUPPORTED;
+  cudaSetDevice(ctx->device);
+  DslashConfig cfg = tuned_dslash(ctx, *gf, prec, long_recon, nrhs, mode, (cudaStream_t)stream);
+  *block = std::min(cfg.block, dslash_max_block(prec, cfg.nr));
+  *rhs_tile = cfg.nr;
+  return SQ_OK;
+}
+
 extern "C" int mdagm_apply(sq_ctx *ctx, int gauge_id, int prec, int long_recon, double mass,
                            const void *in_dev, void *out_dev, void *stream) {
   if (!ctx || !in_dev || !out_dev || in_dev == out_dev || prec < 0 || prec > 2) return SQ_ERR_ARG;
@@ -543,7 +592,10 @@ int solve_batch_locked(sq_ctx *ctx, int gauge_id, int nrhs, const double *src,
   int first_err = SQ_OK;
   bool not_conv = false;
   for (int k = 0; k < nrhs; ++k) {
-    if (stats) fill_stats(w->slots_h[k], secs, gf->g.vh, stats + k);
+    if (stats) {
+      fill_stats(w->slots_h[k], secs, gf->g.vh, stats + k);
+      fill_launch_stats(w, stats + k);
+    }
     int s = slot_status_to_sq(w->slots_h[k].status);
     if (s < 0 && first_err == SQ_OK) first_err = s;
     if (s == SQ_NOT_CONVERGED) not_conv = true;

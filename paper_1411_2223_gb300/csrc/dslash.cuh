@@ -270,13 +270,11 @@ __device__ __forceinline__ void i16_hops(const DslashArgs &a, const LinkScales &
 }
 
 // ------------------------------------------------------ pair at a time
-// One pair of hop matrices (fat or long) is held at a time and applied to
-// every system of the tile, with the hop's sign (eta, backward hop,
-// antiperiodic wrap) folded into the gathered vector.  Used where registers,
-// not the link stream, limit the kernel: FP32 tiles of 8 or 12 systems (each
-// link read once for all of them) and the one-system FP64 kernels (36
-// doubles of links in registers instead of 72, twice the resident warps for
-// an FP64-bound kernel).
+// One pair of hop matrices (fat or long) is held at a time, with the hop's
+// sign (eta, backward hop, antiperiodic wrap) folded into the gathered
+// vector.  Used by the one-system FP64 kernels: 36 doubles of links in
+// registers instead of 72, twice the resident warps for an FP64-bound
+// kernel.
 template <int PREC, int RECON, int NR, int MODE>
 __device__ __forceinline__ void pair_hops(const DslashArgs &a, const LinkScales &ls,
                                           const SiteCoords &sc, int i, int r0,
@@ -314,6 +312,94 @@ __device__ __forceinline__ void pair_hops(const DslashArgs &a, const LinkScales 
               gather_in<PREC, MODE, R>(in, fx, a.xs_prec, S, nb[2 * kind + h], f[2 * kind + h]);
           mat_vec_acc(acc[r], m[h], v);
         }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------ many systems per thread
+// FP32 tiles of NR >= 2 systems.  One hop matrix is held at a time (18
+// floats), the hop's sign (eta, backward hop, antiperiodic wrap) is folded
+// into it once, and it is applied to the gathered neighbour vector of every
+// system of the tile, so the per-system work is the 16 gathers and the
+// 16 x 36 FMAs of the mat-vecs and nothing else.  Holding one matrix
+// instead of a direction's four keeps 12 systems' accumulators in
+// registers.  The matrices of a pair share the middle 16-byte plane of the
+// pair (its first two floats end matrix 0, its last two begin matrix 1).
+template <int RECON, int KIND, int H>
+__device__ __forceinline__ void f32_load_hop(const char *pair, int S, int i, uint64_t pol,
+                                             float (&keep)[2], const LinkScales &ls,
+                                             Mat3<float> &m) {
+  constexpr bool k12 = (KIND == 1 && RECON == 12);
+  constexpr int ne = k12 ? 6 : 9;  // stored elements
+  float f[20];
+  if constexpr (k12) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float4 q = ld_stream_f4(pair + ((size_t)(3 * H + k) * S + i) * 16, pol);
+      f[4 * k] = q.x; f[4 * k + 1] = q.y; f[4 * k + 2] = q.z; f[4 * k + 3] = q.w;
+    }
+  } else if constexpr (H == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const float4 q = ld_stream_f4(pair + ((size_t)k * S + i) * 16, pol);
+      f[4 * k] = q.x; f[4 * k + 1] = q.y; f[4 * k + 2] = q.z; f[4 * k + 3] = q.w;
+    }
+    keep[0] = f[18];
+    keep[1] = f[19];
+  } else {
+    f[0] = keep[0];
+    f[1] = keep[1];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float4 q = ld_stream_f4(pair + ((size_t)(5 + k) * S + i) * 16, pol);
+      f[2 + 4 * k] = q.x; f[3 + 4 * k] = q.y; f[4 + 4 * k] = q.z; f[5 + 4 * k] = q.w;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < ne; ++e) m.e[e] = make_float2(f[2 * e], f[2 * e + 1]);
+  if constexpr (k12) reconstruct_row2(m, ls.recon_f);
+}
+
+template <int RECON, int NR>
+__device__ __forceinline__ void multi_hops(const DslashArgs &a, const LinkScales &ls,
+                                           const SiteCoords &sc, int i, int r0,
+                                           const bool (&active)[NR], Vec3<float> (&acc)[NR]) {
+  using LL = LinkLayout<PREC_F32, RECON>;
+  const Geom &g = a.g;
+  const int S = g.stride;
+  const uint64_t pol = l2_link_policy(ls.keep);
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+    int nb[4];
+    float f[4];
+    nb[0] = hop<+1>(g, sc, mu, f[0]);
+    nb[1] = hop<-1>(g, sc, mu, f[1]);
+    nb[2] = hop<+3>(g, sc, mu, f[2]);
+    nb[3] = hop<-3>(g, sc, mu, f[3]);
+    const float eta = eta_sign(sc, mu);
+    f[0] *= eta;
+    f[1] *= -eta;
+    f[2] *= eta;
+    f[3] *= -eta;
+    const char *fat = a.links + (size_t)mu * LL::mu_bytes * S;
+    const char *lng = fat + (size_t)LL::fat_bytes * S;
+    float keep[2];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      Mat3<float> m;
+      if (h == 0) f32_load_hop<RECON, 0, 0>(fat, S, i, pol, keep, ls, m);
+      else if (h == 1) f32_load_hop<RECON, 0, 1>(fat, S, i, pol, keep, ls, m);
+      else if (h == 2) f32_load_hop<RECON, 1, 0>(lng, S, i, pol, keep, ls, m);
+      else f32_load_hop<RECON, 1, 1>(lng, S, i, pol, keep, ls, m);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) { m.e[e].x *= f[h]; m.e[e].y *= f[h]; }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (!active[r]) continue;
+        const Vec3<float> v =
+            SpinorIO<PREC_F32>::load(a.in + (size_t)(r0 + r) * a.in_fb, S, nb[h]);
+        mat_vec_acc(acc[r], m, v);
       }
     }
   }
@@ -385,7 +471,7 @@ dslash_kernel(const DslashArgs a) {
   // kernel lets its successor launch only after its own wait, so that one
   // has completed).
   FirstLinks<PREC, RECON> first;
-  constexpr bool kFirst = FirstLinks<PREC, RECON>::kUsed && (PREC == PREC_I16 || NR < 8);
+  constexpr bool kFirst = FirstLinks<PREC, RECON>::kUsed && (PREC == PREC_I16 || NR == 1);
   if constexpr (kFirst) {
     if (i < g.vh) first.load(a, ls, i);
   }
@@ -450,7 +536,9 @@ dslash_kernel(const DslashArgs a) {
     const SiteCoords sc = site_coords(g, a.out_parity, i);
     if constexpr (PREC == PREC_I16) {
       i16_hops<RECON, NR>(a, ls, sc, i, r0, active, acc, first.buf);
-    } else if constexpr ((PREC == PREC_F32 && NR >= 8) || (PREC == PREC_F64 && NR == 1)) {
+    } else if constexpr (PREC == PREC_F32 && NR >= 2) {
+      multi_hops<RECON, NR>(a, ls, sc, i, r0, active, acc);
+    } else if constexpr (PREC == PREC_F64 && NR == 1) {
       pair_hops<PREC, RECON, NR, MODE>(a, ls, sc, i, r0, active, acc);
     } else {
 #pragma unroll 1

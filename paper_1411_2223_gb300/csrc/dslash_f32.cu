@@ -13,7 +13,7 @@ int launch_dslash_f32(int recon, int nr, int mode, int outp, const DslashArgs &a
                    cudaSuccess ? 0 : -1; \
   }
 #define SQ_K_NR(RC, MODE, OUTP) SQ_K(RC, 1, MODE, OUTP) SQ_K(RC, 2, MODE, OUTP) SQ_K(RC, 4, MODE, OUTP) \
-  SQ_K(RC, 8, MODE, OUTP) SQ_K(RC, 12, MODE, OUTP)
+  SQ_K(RC, 6, MODE, OUTP) SQ_K(RC, 8, MODE, OUTP) SQ_K(RC, 12, MODE, OUTP)
   SQ_K_NR(18, MODE_PLAIN, PREC_F32)
   SQ_K_NR(12, MODE_PLAIN, PREC_F32)
   SQ_K_NR(18, MODE_MDAGM, PREC_F32)

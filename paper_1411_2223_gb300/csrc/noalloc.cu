@@ -2,13 +2,12 @@
 // kernels as mdagm_apply) with its odd-parity temporary in a fixed device
 // array owned by this library, so that a call allocates nothing.
 //
-// Who needs it: code that must not allocate device memory at call time --
-// work recorded into a CUDA graph by stream capture (an allocation there is
-// illegal or breaks the capture), applications that reserve all of HBM up
-// front through their own allocator or memory pool and forbid libraries to
-// allocate behind it, and latency-critical loops where a first-use
-// cudaMalloc would be an unpredictable stall.  mdagm_apply, by contrast,
-// allocates its temporary on first use per gauge field and precision.
+// Who needs it: callers that cannot let the library allocate device memory
+// at call time -- applications that reserve all of HBM up front through
+// their own allocator or memory pool and forbid libraries to allocate behind
+// it, and latency-critical loops where a first-use cudaMalloc would be an
+// unpredictable stall.  mdagm_apply, by contrast, allocates its temporary on
+// first use per gauge field and precision.
 //
 // The array is a file-scope __device__ variable: every GPU on which the
 // library is loaded holds SQ_STATIC_SCRATCH_BYTES of it until the process
@@ -30,7 +29,8 @@ std::mutex g_scratch_mu;
 void *g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on `device` (current device), looked
-// up on the first call for that device.
+// up on the first call for that device (a one-time set-up: that first call
+// should come before any stream capture).
 int scratch_address(int device, void **out) {
   if (device < 0 || device >= kMaxDevices) return SQ_ERR_ARG;
   std::lock_guard<std::mutex> lk(g_scratch_mu);

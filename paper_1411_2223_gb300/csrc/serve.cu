@@ -112,6 +112,7 @@ static void finish_request(ServeEngine *e, Batch &b, int s) {
   auto now = Clock::now();
   double secs = std::chrono::duration<double>(now - req->t_submit).count();
   fill_stats(ss, secs, b.gf->g.vh, &req->stats);
+  fill_launch_stats(b.w, &req->stats);
   {
     std::lock_guard<std::mutex> lk(e->mu);
     req->status = req->stats.status;

@@ -19,6 +19,7 @@
 // wasted.  k iterations are captured once into a CUDA graph and replayed; the
 // host reads the slot states after each replay.  Finished slots make every
 // kernel skip their work, so overshooting the last block costs launches only.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -306,8 +307,17 @@ int slot_status_to_sq(int s) {
   }
 }
 
+void fill_launch_stats(const CGWork *w, sq_cg_stats *st) {
+  if (!st) return;
+  st->oe_block = std::min(w->cfg_norm.block, dslash_max_block(w->prec, w->cfg_norm.nr));
+  st->oe_rhs_tile = w->cfg_norm.nr;
+  st->eo_block = std::min(w->cfg_update.block, dslash_max_block(w->prec, w->cfg_update.nr));
+  st->eo_rhs_tile = w->cfg_update.nr;
+}
+
 void fill_stats(const SlotState &s, double seconds, long vh, sq_cg_stats *st) {
   if (!st) return;
+  std::memset(st, 0, sizeof(*st));
   st->status = slot_status_to_sq(s.status);
   st->iterations = s.iter;
   st->reliable_updates = s.n_ru;

@@ -133,5 +133,7 @@ int slot_status_to_sq(int slot_status);
 inline bool cg_slot_live(int s) { return s == SLOT_RUNNING || s == SLOT_WAIT || s == SLOT_INIT; }
 void drop_multishift_works(const sq_ctx *ctx, int gauge_id);  // gauge_id < 0: all
 void fill_stats(const SlotState &s, double seconds, long vh, sq_cg_stats *st);
+// The launch shapes of the workspace's two sloppy Dslash kernels.
+void fill_launch_stats(const CGWork *w, sq_cg_stats *st);
 
 }  // namespace sq

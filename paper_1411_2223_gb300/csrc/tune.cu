@@ -27,7 +27,7 @@ struct Tuner {
 
 static std::string tune_key(const Geom &g, int prec, int recon, int nrhs, int mode) {
   std::ostringstream s;
-  s << "dslash_v3:" << g.L[0] << "x" << g.L[1] << "x" << g.L[2] << "x" << g.L[3] << ":p" << prec
+  s << "dslash_v4:" << g.L[0] << "x" << g.L[1] << "x" << g.L[2] << "x" << g.L[3] << ":p" << prec
     << ":r" << recon << ":n" << nrhs << ":m" << mode;
   return s.str();
 }
@@ -53,13 +53,116 @@ static void tuner_save(Tuner *t) {
   for (auto &kv : t->cache) out << kv.first << " " << kv.second.block << " " << kv.second.nr << "\n";
 }
 
+// Device buffers and arguments of one Dslash kernel on synthetic inputs, for
+// timing it alone: the gauge field's own links, zero-filled vector fields
+// with a finite non-zero input, and, for the reducing epilogues, running
+// systems that the timed launches cannot stop (no convergence, no max_iter,
+// no reliable update).
+struct KernelBench {
+  void *in = nullptr, *out = nullptr, *aux = nullptr;
+  DslashArgs a;
+  ~KernelBench() {
+    if (in) cudaFree(in);
+    if (out) cudaFree(out);
+    if (aux) cudaFree(aux);
+  }
+  bool setup(const GaugeField &gf, int prec, int recon, int nrhs, int mode, cudaStream_t st) {
+    const bool reduces = mode != MODE_PLAIN;
+    const Geom &g = gf.g;
+    const size_t fb = spinor_bytes(prec, g.stride);
+    // aux: the p field, slot states, partial sums, the ticket counters and
+    // the solution increment xs, each 256-byte aligned
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t xs_b = spinor_bytes(xs_prec(prec), g.stride) * nrhs;
+    const size_t o_slots = al(fb * nrhs);
+    const size_t o_part = o_slots + al(sizeof(SlotState) * nrhs);
+    const size_t o_cnt = o_part + al(sizeof(double) * 3 * nrhs * red_stride(g));
+    const size_t o_xs = o_cnt + al(sizeof(unsigned) * nrhs * ticket_stride(g));
+    const size_t aux_b = o_xs + al(xs_b);
+    if (cudaMalloc(&in, fb * nrhs) != cudaSuccess || cudaMalloc(&out, fb * nrhs) != cudaSuccess ||
+        cudaMalloc(&aux, aux_b) != cudaSuccess)
+      return false;
+    // input: a finite non-zero byte pattern (about 0.01 in FP32)
+    cudaMemsetAsync(in, 0x3c, fb * nrhs, st);
+    cudaMemsetAsync(out, 0, fb * nrhs, st);
+    cudaMemsetAsync(aux, 0, aux_b, st);
+    char *auxc = static_cast<char *>(aux);
+    SlotState *slots = reinterpret_cast<SlotState *>(auxc + o_slots);
+    if (reduces) {
+      std::vector<SlotState> hs(nrhs);
+      for (auto &s : hs) {
+        std::memset(&s, 0, sizeof(s));
+        s.status = SLOT_RUNNING;
+        s.m2 = 1e-4;
+        s.rr = 1.0;
+        s.tol2b2 = -1.0;
+        s.max_iter = 1 << 30;
+      }
+      if (cudaMemcpyAsync(slots, hs.data(), sizeof(SlotState) * nrhs, cudaMemcpyHostToDevice,
+                          st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return false;
+    }
+    std::memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.out_parity = 1;
+    a.links = gf.link_ptr(prec, recon, 1);
+    a.ls = gf.scales(prec, recon);
+    a.in = static_cast<const char *>(in);
+    a.out = static_cast<char *>(out);
+    a.in_fb = a.out_fb = fb;
+    a.nrhs = nrhs;
+    a.gate = GATE_NONE;
+    if (reduces) {
+      a.slots = slots;
+      a.partial = reinterpret_cast<double *>(auxc + o_part);
+      a.counter = reinterpret_cast<unsigned *>(auxc + o_cnt);
+      a.gate = GATE_RUNNING;
+    }
+    if (mode == MODE_MDAGM || mode == MODE_UPDATE) {
+      a.out_parity = 0;
+      a.links = gf.link_ptr(prec, recon, 0);
+      a.p = auxc;
+      a.p_fb = fb;
+    }
+    if (mode == MODE_UPDATE) {
+      a.xs = auxc + o_xs;
+      a.xs_fb = spinor_bytes(xs_prec(prec), g.stride);
+      a.xs_prec = xs_prec(prec);
+    }
+    return true;
+  }
+};
+
+// Milliseconds per launch of `reps` back-to-back launches (CUDA events on
+// `st`) after one untimed launch; negative if the shape cannot launch.
+static float time_launches(KernelBench &kb, int prec, int recon, int nr, int mode, int block,
+                           int reps, cudaStream_t st, sq_ctx *ctx) {
+  if (launch_dslash(prec, recon, nr, mode, prec, kb.a, block, st) != 0) return -1.f;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  for (int k = 0; k < reps; ++k) launch_dslash(prec, recon, nr, mode, prec, kb.a, block, st);
+  cudaEventRecord(e1, st);
+  float ms = -1.f;
+  if (cudaEventSynchronize(e1) == cudaSuccess) {
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->launches += reps + 1;
+  if (cudaGetLastError() != cudaSuccess) return -1.f;
+  return ms;
+}
+
 DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon, int nrhs,
                           int mode, cudaStream_t st) {
   // PLAIN and the reduction epilogues (MDAGM, NORM, UPDATE) are tuned apart:
   // a reduction favours more, smaller blocks per SM.  RESID uses the PLAIN
   // shape.
   if (mode != MODE_MDAGM && mode != MODE_NORM && mode != MODE_UPDATE) mode = MODE_PLAIN;
-  const bool reduces = mode != MODE_PLAIN;
   DslashConfig def;
   def.block = 256;
   def.nr = nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1;
@@ -72,109 +175,55 @@ DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon
   cudaStreamCaptureStatus cs;
   if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
     return def;
-
-  const Geom &g = gf.g;
-  size_t fb = spinor_bytes(prec, g.stride);
-  void *in = nullptr, *out = nullptr, *aux = nullptr;
-  // aux: p field, slot states, partial sums, the ticket counters and (UPDATE)
-  // the solution increment xs
-  const size_t xs_b = spinor_bytes(xs_prec(prec), g.stride) * nrhs;
-  size_t aux_b = fb * nrhs + sizeof(SlotState) * nrhs + sizeof(double) * nrhs * red_stride(g) +
-                 sizeof(unsigned) * nrhs * ticket_stride(g) + 256 + xs_b;
-  if (cudaMalloc(&in, fb * nrhs) != cudaSuccess) return def;
-  if (cudaMalloc(&out, fb * nrhs) != cudaSuccess || cudaMalloc(&aux, aux_b) != cudaSuccess) {
-    cudaFree(in);
-    if (out) cudaFree(out);
-    return def;
-  }
-  cudaMemsetAsync(in, 0, fb * nrhs, st);
-  cudaMemsetAsync(aux, 0, aux_b, st);
-  char *auxc = static_cast<char *>(aux);
-  SlotState *slots = reinterpret_cast<SlotState *>(auxc + fb * nrhs);
-  double *partial = reinterpret_cast<double *>(slots + nrhs);
-  unsigned *counter = reinterpret_cast<unsigned *>(partial + (size_t)nrhs * red_stride(g));
-  // xs at the end, 256-byte aligned: rounding the offset down stays inside
-  // the 256 spare bytes after the counters
-  char *xs = auxc + (aux_b - xs_b) / 256 * 256;
-  if (reduces) {
-    // running systems that the timed launches cannot stop (an UPDATE epilogue
-    // never sees convergence or max_iter)
-    std::vector<SlotState> hs(nrhs);
-    for (auto &s : hs) {
-      std::memset(&s, 0, sizeof(s));
-      s.status = SLOT_RUNNING;
-      s.m2 = 1e-4;
-      s.rr = 1.0;
-      s.tol2b2 = -1.0;
-      s.max_iter = 1 << 30;
-    }
-    cudaMemcpyAsync(slots, hs.data(), sizeof(SlotState) * nrhs, cudaMemcpyHostToDevice, st);
-  }
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  DslashArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.g = g;
-  a.out_parity = 1;
-  a.links = gf.link_ptr(prec, recon, 1);
-  a.ls = gf.scales(prec, recon);
-  a.in = static_cast<const char *>(in);
-  a.out = static_cast<char *>(out);
-  a.in_fb = a.out_fb = fb;
-  a.nrhs = nrhs;
-  a.gate = GATE_NONE;
-  if (reduces) {
-    a.slots = slots;
-    a.partial = partial;
-    a.counter = counter;
-    a.gate = GATE_RUNNING;
-  }
-  if (mode == MODE_MDAGM || mode == MODE_UPDATE) {
-    a.out_parity = 0;
-    a.links = gf.link_ptr(prec, recon, 0);
-    a.p = auxc;
-    a.p_fb = fb;
-  }
-  if (mode == MODE_UPDATE) {
-    a.xs = xs;
-    a.xs_fb = spinor_bytes(xs_prec(prec), g.stride);
-    a.xs_prec = xs_prec(prec);
-  }
-  // RHS tiles; the many-RHS tiles (8, 12) exist for the FP32 kernels only
+  KernelBench kb;
+  if (!kb.setup(gf, prec, recon, nrhs, mode, st)) return def;
+  // RHS tiles; the many-RHS tiles (6, 8, 12) exist for the FP32 kernels only
   // (launch_dslash refuses the others and the candidate is skipped)
   std::vector<int> nrs = {1};
-  for (int nr : {2, 4, 8, 12})
+  for (int nr : {2, 4, 6, 8, 12})
     if (nrhs >= nr) nrs.push_back(nr);
   float best = 1e30f;
   DslashConfig best_c = def;
-  const int reps = 5;
   for (int nr : nrs) {
     const int max_block = dslash_max_block(prec, nr);
     for (int block = 128; block <= max_block; block += 128) {
-      if (launch_dslash(prec, recon, nr, mode, prec, a, block, st) != 0) continue;
-      cudaEventRecord(e0, st);
-      for (int k = 0; k < reps; ++k) launch_dslash(prec, recon, nr, mode, prec, a, block, st);
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) continue;
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ctx->launches += reps + 1;
-      if (cudaGetLastError() == cudaSuccess && ms < best) {
+      const float ms = time_launches(kb, prec, recon, nr, mode, block, 5, st, ctx);
+      if (ms >= 0.f && ms < best) {
         best = ms;
         best_c.block = block;
         best_c.nr = nr;
       }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaFree(in);
-  cudaFree(out);
-  cudaFree(aux);
   t->cache[key] = best_c;
   tuner_save(t);
   return best_c;
 }
 
 }  // namespace sq
+
+using namespace sq;
+
+extern "C" int sq_time_dslash(sq_ctx *ctx, int gauge_id, int prec, int long_recon, int nrhs,
+                              int mode, int reps, void *stream, float *us_per_launch) {
+  if (!ctx || !us_per_launch || prec < 0 || prec > 2 || reps < 1) return SQ_ERR_ARG;
+  if (long_recon != 18 && long_recon != 12) return SQ_ERR_ARG;
+  if (nrhs < 1 || nrhs > 64) return SQ_ERR_ARG;
+  if (mode != MODE_PLAIN && mode != MODE_MDAGM && mode != MODE_NORM && mode != MODE_UPDATE)
+    return SQ_ERR_ARG;
+  GaugeField *gf = ctx->gauge(gauge_id);
+  if (!gf) return SQ_ERR_NOTFOUND;
+  if (!gf->has(prec, long_recon)) return SQ_ERR_UNSUPPORTED;
+  SQ_CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const DslashConfig cfg = tuned_dslash(ctx, *gf, prec, long_recon, nrhs, mode, st);
+  KernelBench kb;
+  if (!kb.setup(*gf, prec, long_recon, nrhs, mode, st)) return SQ_ERR_OOM;
+  for (int k = 0; k < 4; ++k)  // warm-up
+    if (launch_dslash(prec, long_recon, cfg.nr, mode, prec, kb.a, cfg.block, st)) return SQ_ERR_ARG;
+  ctx->launches += 4;
+  const float ms = time_launches(kb, prec, long_recon, cfg.nr, mode, cfg.block, reps, st, ctx);
+  if (ms < 0.f) return SQ_ERR_CUDA;
+  *us_per_launch = ms * 1e3f;
+  return SQ_OK;
+}

@@ -53,7 +53,9 @@ class CgOpts(ctypes.Structure):
 class CgStats(ctypes.Structure):
     _fields_ = [('status', ctypes.c_int), ('iterations', ctypes.c_int),
                 ('reliable_updates', ctypes.c_int), ('true_residual', ctypes.c_double),
-                ('seconds', ctypes.c_double), ('gflops', ctypes.c_double)]
+                ('seconds', ctypes.c_double), ('gflops', ctypes.c_double),
+                ('oe_block', ctypes.c_int), ('oe_rhs_tile', ctypes.c_int),
+                ('eo_block', ctypes.c_int), ('eo_rhs_tile', ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +91,10 @@ SIGNATURES = {
     'sq_pack_spinor': (_I, [_P, _I, _I, _P, _P, _P]),
     'sq_unpack_spinor': (_I, [_P, _I, _I, _P, _P, _P]),
     'dslash_apply': (_I, [_P, _I, _I, _I, _I, _P, _P, _P]),
+    'dslash_apply_multi': (_I, [_P, _I, _I, _I, _I, _I, _P, _P, _P]),
+    'sq_tuned_launch': (_I, [_P, _I, _I, _I, _I, _I, _P, ctypes.POINTER(_I),
+                             ctypes.POINTER(_I)]),
+    'sq_time_dslash': (_I, [_P, _I, _I, _I, _I, _I, _I, _P, ctypes.POINTER(ctypes.c_float)]),
     'mdagm_apply': (_I, [_P, _I, _I, _I, _D, _P, _P, _P]),
     'mdagm_apply_static': (_I, [_P, _I, _I, _I, _D, _P, _P, _P]),
     'cg_solve': (_I, [_P, _I, _P, _D, _D, ctypes.POINTER(CgOpts), _P, ctypes.POINTER(CgStats)]),
@@ -276,6 +282,36 @@ class Context:
         _check(self._lib.dslash_apply(self.handle, gauge_id, int(out_parity), PREC[prec],
                                       int(long_recon), _ptr(in_dev), _ptr(out_dev),
                                       _stream(stream)), 'dslash_apply')
+
+    def dslash_apply_multi(self, gauge_id, out_parity, prec, long_recon, nrhs, in_dev, out_dev,
+                           stream=None):
+        """out_j = D in_j for nrhs packed vectors back to back (device)."""
+        _check(self._lib.dslash_apply_multi(self.handle, gauge_id, int(out_parity), PREC[prec],
+                                            int(long_recon), int(nrhs), _ptr(in_dev),
+                                            _ptr(out_dev), _stream(stream)),
+               'dslash_apply_multi')
+
+    MODES = {'plain': 0, 'mdagm': 1, 'cg_oe': 3, 'cg_eo': 4}
+
+    def tuned_launch(self, gauge_id, prec, long_recon, nrhs, mode, stream=None):
+        """(threads per block, right-hand sides per thread) the library
+        launches a Dslash kernel with; mode in MODES (or its number)."""
+        b, t = ctypes.c_int(0), ctypes.c_int(0)
+        m = self.MODES.get(mode, mode)
+        _check(self._lib.sq_tuned_launch(self.handle, gauge_id, PREC[prec], int(long_recon),
+                                         int(nrhs), int(m), _stream(stream), ctypes.byref(b),
+                                         ctypes.byref(t)), 'sq_tuned_launch')
+        return b.value, t.value
+
+    def time_dslash(self, gauge_id, prec, long_recon, nrhs, mode, reps=50, stream=None):
+        """Microseconds per launch of a Dslash kernel at the library's launch
+        shape (CUDA events, back-to-back launches on synthetic vectors)."""
+        us = ctypes.c_float(0)
+        m = self.MODES.get(mode, mode)
+        _check(self._lib.sq_time_dslash(self.handle, gauge_id, PREC[prec], int(long_recon),
+                                        int(nrhs), int(m), int(reps), _stream(stream),
+                                        ctypes.byref(us)), 'sq_time_dslash')
+        return float(us.value)
 
     def mdagm_apply(self, gauge_id, prec, long_recon, mass, in_dev, out_dev, stream=None):
         _check(self._lib.mdagm_apply(self.handle, gauge_id, PREC[prec], int(long_recon),
@@ -517,7 +553,8 @@ def _forward(name):
     return f
 
 
-for _n in ('gauge_load', 'gauge_free', 'gauge_fatten', 'gauge_load_thin', 'gauge_fatten_asqtad', 'dslash_apply', 'mdagm_apply', 'cg_solve',
+for _n in ('gauge_load', 'gauge_free', 'gauge_fatten', 'gauge_load_thin', 'gauge_fatten_asqtad',
+           'dslash_apply', 'dslash_apply_multi', 'mdagm_apply', 'cg_solve',
            'cg_solve_multi', 'cg_solve_multishift', 'cg_solve_full', 'bicgstab_solve_full',
            'dirac_apply',
            'npr_four_fermion', 'serve_submit', 'serve_poll',

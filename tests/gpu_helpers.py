@@ -21,6 +21,15 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
+def site_rel(a, b):
+    """Largest error of one site's colour vector, relative to the RMS site
+    norm of b: unlike rel(), one wrong site among 10^5 fails it."""
+    a = np.asarray(a).reshape(-1, 3)
+    b = np.asarray(b).reshape(-1, 3)
+    err = np.linalg.norm(a - b, axis=1).max()
+    return float(err / np.sqrt(np.mean(np.sum(np.abs(b) ** 2, axis=1))))
+
+
 def to_dev(a):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).cuda()
@@ -29,11 +38,10 @@ def to_dev(a):
 def packed_buffer(ctx, gid, prec):
     import torch
     nbytes, _ = ctx.spinor_bytes(gid, prec)
-    buf = torch.zeros(nbytes, dtype=torch.uint8, device='cuda')
-    # the library's calls without a stream run on the context's own stream:
-    # the zero fill must be done before they write
-    torch.cuda.synchronize()
-    return buf
+    # the library's asynchronous calls without a stream run on the legacy
+    # default stream, which is torch's default stream too: they are ordered
+    # after this fill
+    return torch.zeros(nbytes, dtype=torch.uint8, device='cuda')
 
 
 def pack(ctx, gid, prec, v_half):

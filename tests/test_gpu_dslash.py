@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_helpers import TOL_DSLASH, gauge, gpu_dslash, gpu_mdagm, pack, rel, unpack
+from gpu_helpers import TOL_DSLASH, gauge, gpu_dslash, gpu_mdagm, pack, rel, site_rel, unpack
 
 pytestmark = pytest.mark.gpu
 
@@ -151,6 +151,8 @@ def test_dslash_full_size_20x64(sq, prec):
         for recon in (18, 12):
             got = gpu_dslash(sq, gid, prec, recon, v, 1, vh)
             assert rel(got, want) <= TOL_DSLASH[prec], (recon, rel(got, want))
+            # and site by site: one wrong site among the 256000 fails this
+            assert site_rel(got, want) <= TOL_DSLASH[prec], (recon, site_rel(got, want))
     finally:
         sq.gauge_free(gid)
 
@@ -173,5 +175,38 @@ def test_gauge_load_rejects_bad_input(sq):
         with pytest.raises(sqm.SqError) as e:
             gpu_dslash(sq, gid, 'f32', 12, synth.gaussian_source(128, 0), 0, 128)
         assert e.value.status == sqm.ERR_UNSUPPORTED
+    finally:
+        sq.gauge_free(gid)
+
+
+def test_null_stream_is_the_legacy_default_stream(sq):
+    """The asynchronous calls run on the stream they are given, and NULL is
+    the legacy default stream (torch's default stream).  Work queued before
+    them -- here the copy of the input, held back by a spin of about 50 ms
+    on the GPU -- is therefore done before they read, on the default stream
+    and on a torch side stream alike."""
+    import contextlib
+    import torch
+    dims = (8, 8, 8, 8)
+    fat, lng = gauge(dims, 0.25, 0)
+    vh = oracle.volume(dims) // 2
+    v = synth.gaussian_source(vh, 3)
+    want = oracle.dslash_half(dims, fat, lng, v, 1)
+    gid = sq.gauge_load(dims, fat, lng)
+    try:
+        src = pack(sq, gid, 'f32', v)
+        torch.cuda.synchronize()
+        for side in (False, True):
+            stream = torch.cuda.Stream() if side else None
+            with torch.cuda.stream(stream) if side else contextlib.nullcontext():
+                inp = torch.zeros_like(src)
+                out = torch.zeros_like(src)
+                canon = torch.zeros((vh, 3), dtype=torch.complex128, device='cuda')
+                torch.cuda._sleep(100_000_000)
+                inp.copy_(src)
+                sq.dslash_apply(gid, 1, 'f32', 18, inp, out, stream=stream)
+                sq.unpack_spinor(gid, 'f32', out, canon, stream=stream)
+                got = canon.cpu().numpy()
+            assert rel(got, want) <= TOL_DSLASH['f32'], (side, rel(got, want))
     finally:
         sq.gauge_free(gid)

@@ -147,10 +147,12 @@ def test_batched_full_size_24x64(sq):
 @pytest.mark.parametrize('recon', [18, 12])
 def test_many_rhs_tiles_match_oracle(tmp_path, monkeypatch, nr, recon):
     """The FP32 Dslash tiles that apply each link to 8 or 12 systems, forced
-    through a tuning cache file (SQ_TUNE_CACHE), solve every system of a
-    12-system batch to the oracle's acceptance, in the iteration counts of
-    the one-system tile (the two tiles add the 16 hop products in different
-    orders, so they agree to rounding, not bit for bit)."""
+    through a tuning cache file (SQ_TUNE_CACHE) onto both kernels of the CG
+    iteration (the D_oe kernel with the reduction, mode 3, and the D_eo kernel
+    with the update, mode 4), solve every system of a 12-system batch to the
+    oracle's acceptance, in the iteration counts of the one-system tile (the
+    two tiles add the 16 hop products in different orders, so they agree to
+    rounding, not bit for bit).  The solve reports the tiles it launched."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip('no CUDA device')
@@ -166,16 +168,69 @@ def test_many_rhs_tiles_match_oracle(tmp_path, monkeypatch, nr, recon):
     results = {}
     for tile in (1, nr):
         cache = tmp_path / ('tune_%d.txt' % tile)
-        cache.write_text(''.join('dslash_v3:%s:p1:r%d:n%d:m%d 128 %d\n' % (lat, recon, nrhs, m, tile)
-                                 for m in (0, 1)))
+        cache.write_text(''.join('dslash_v4:%s:p1:r%d:n%d:m%d 128 %d\n' % (lat, recon, nrhs, m, tile)
+                                 for m in (3, 4)))
         monkeypatch.setenv('SQ_TUNE_CACHE', str(cache))
         with sqm.Context(0) as ctx:
             gid = ctx.gauge_load(dims, fat, lng)
             xs, stats, status = ctx.cg_solve_multi(gid, srcs, masses, tol, long_recon=recon)
             assert status == 0
+        for s in stats:
+            assert (s['oe_rhs_tile'], s['eo_rhs_tile']) == (tile, tile), s
+            assert (s['oe_block'], s['eo_block']) == (128, 128), s
         results[tile] = (xs, [s['iterations'] for s in stats])
     xs, its = results[nr]
     assert max(abs(a - b) for a, b in zip(its, results[1][1])) <= 4
     for j in range(nrhs):
         x_ref, _, _ = oracle.cg(dims, fat, lng, masses[j], srcs[j], 1e-12)
         o9_check(dims, fat, lng, masses[j], srcs[j], xs[j], x_ref, tol)
+
+
+TILES = {'f32': (1, 2, 4, 6, 8, 12), 'f64': (1, 2, 4), 'i16': (1, 2, 4)}
+
+
+@pytest.mark.parametrize('prec', ['f32', 'f64', 'i16'])
+@pytest.mark.parametrize('recon', [18, 12])
+def test_batched_dslash_every_tile_matches_oracle(tmp_path, monkeypatch, prec, recon):
+    """dslash_apply_multi on 12 right-hand sides with each tile of
+    right-hand sides per thread forced through SQ_TUNE_CACHE: every system's
+    output matches the oracle's Dslash on the unquantised input, in norm and
+    site by site (a 2 x 6 x 4 x 10 lattice: 240 sites per parity, ragged
+    against every block, several tiles of the 12 systems and a partial last
+    one), and sq_tuned_launch reports the forced shape."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip('no CUDA device')
+    from paper_1411_2223_gb300 import sq as sqm
+    from gpu_helpers import TOL_DSLASH, rel, site_rel
+    dims = (2, 6, 4, 10)
+    fat, lng = gauge(dims, 0.25, 0)
+    vh = oracle.volume(dims) // 2
+    nrhs = 12
+    srcs = synth.gaussian_sources(vh, range(40, 40 + nrhs))
+    lat = 'x'.join(map(str, dims))
+    want = [[oracle.dslash_half(dims, fat, lng, srcs[j], par) for j in range(nrhs)]
+            for par in (0, 1)]
+    for tile in TILES[prec]:
+        cache = tmp_path / ('tune_%s_%d.txt' % (prec, tile))
+        cache.write_text('dslash_v4:%s:p%d:r%d:n%d:m0 128 %d\n'
+                         % (lat, sqm.PREC[prec], recon, nrhs, tile))
+        monkeypatch.setenv('SQ_TUNE_CACHE', str(cache))
+        with sqm.Context(0) as ctx:
+            gid = ctx.gauge_load(dims, fat, lng)
+            assert ctx.tuned_launch(gid, prec, recon, nrhs, 'plain') == (128, tile)
+            nbytes, _ = ctx.spinor_bytes(gid, prec)
+            src = torch.zeros(nrhs * nbytes, dtype=torch.uint8, device='cuda')
+            dst = torch.zeros_like(src)
+            for j in range(nrhs):
+                ctx.pack_spinor(gid, prec, torch.from_numpy(srcs[j]).cuda(),
+                                src[j * nbytes:(j + 1) * nbytes])
+            for par in (0, 1):
+                ctx.dslash_apply_multi(gid, par, prec, recon, nrhs, src, dst)
+                for j in range(nrhs):
+                    canon = torch.zeros((vh, 3), dtype=torch.complex128, device='cuda')
+                    ctx.unpack_spinor(gid, prec, dst[j * nbytes:(j + 1) * nbytes], canon)
+                    got = canon.cpu().numpy()
+                    w = want[par][j]
+                    assert rel(got, w) <= TOL_DSLASH[prec], (tile, par, j, rel(got, w))
+                    assert site_rel(got, w) <= TOL_DSLASH[prec], (tile, par, j)

@@ -1,8 +1,9 @@
 """mdagm_apply_static: the allocation-free form of the CG operator.
 
-Some callers cannot allocate device memory when they call the library
-(stream capture, an application-owned memory pool, latency-critical loops),
-so this entry point keeps its temporary in a fixed device array.  Through the
+Some callers cannot let the library allocate device memory when they call
+it (an application that owns all of HBM through its own memory pool, a
+latency-critical loop that cannot take a first-use cudaMalloc), so this
+entry point keeps its temporary in a fixed device array.  Through the
 C ABI, two calls in a row must reproduce mdagm_apply (same kernels: the
 results are compared within the Dslash tolerances and are expected to agree
 bit for bit), and a lattice whose temporary does not fit the array must be
