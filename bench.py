@@ -36,6 +36,11 @@ EPS, GAUGE_SEED, SRC_SEED, MASS, TOL = 0.25, 0, 0, 0.01, 1e-8
 DSLASH_BYTES = {('f64', 18): 2400, ('f64', 12): 2016, ('f32', 18): 1200, ('f32', 12): 1008,
                 ('i16', 18): 608, ('i16', 12): 512}
 DSLASH_FLOPS = 1146
+# Algorithmic bytes per output site of the CG's two FP32 18-real kernels:
+# D_oe p with <p, A p>: links 1152 + p in 24 + t out 24 (the own-site p is
+# the same input field); D_eo t with the update: links 1152 + t 24 + p 24 +
+# r in/out 48 + xs in/out 48.  The separate xpay kernel moves 72 B per site.
+CG_KERNEL_BYTES = {'cg_oe': 1200, 'cg_eo': 1296}
 CG_FLOPS_PER_SITE_ITER = 2364
 PAPER_CONTEXT_GFLOPS = 46.48   # mixed-precision CG, GTX Titan Black (Table 2)
 # DRAM traffic of one FP32 18-real Dslash launch at 20^3 x 64 from an ncu
@@ -167,25 +172,50 @@ def cpu_baseline(fat, lng, b, sample_s):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle on the host cores.  A step is a
+    bounded sample of the workload -- n oracle FP64 CG iterations on the
+    20^3 x 64 system, n chosen so that the warm-up and timed steps take about
+    90 s -- so ms_per_step is the measured time of a step.  `value`, in the
+    metric's unit (ms to solve to 1e-8), is one complete oracle solve to
+    1e-8, timed after the steps; the per-iteration extrapolation is kept as
+    a labelled extra."""
     rank = int(os.environ.get('RANK', '0'))
     if rank != 0:
         return 0
     import numpy as np  # noqa: F401
+    import oracle
     import synth
     fat, lng = synth.gauge_field(DIMS, EPS, GAUGE_SEED)
     b = synth.gaussian_source(int(np.prod(DIMS)) // 2, SRC_SEED)
-    vals = []
+    t0 = time.time()
+    oracle.cg(DIMS, fat, lng, MASS, b, TOL, max_iter=2)
+    per_iter = (time.time() - t0) / 3.0          # 2 iterations + the final true residual
+    n = max(1, int(90.0 / (args.warmup + args.steps) / per_iter) - 1)
+    step_ms = []
     for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(fat, lng, b, args.cpu_sample_s / 3)
+        t0 = time.perf_counter()
+        oracle.cg(DIMS, fat, lng, MASS, b, TOL, max_iter=n)
+        dt = (time.perf_counter() - t0) * 1e3
         if k >= args.warmup:
-            vals.append(cb['value'])
-    v = statistics.median(vals)
-    line = {'impl': 'reference', 'metric': METRIC, 'value': v, 'unit': 'ms', 'n_gpus': args.gpus,
-            'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': v,
+            step_ms.append(dt)
+    ms_step = statistics.median(step_ms)
+    t0 = time.perf_counter()
+    _, iters, res = oracle.cg(DIMS, fat, lng, MASS, b, TOL)
+    full_ms = (time.perf_counter() - t0) * 1e3
+    cores = int(os.environ.get('OMP_NUM_THREADS', os.cpu_count() or 1))
+    sample = ('a step is %d oracle FP64 CG iterations (+ the final FP64 residual) on the '
+              '20^3x64 workload; value is one complete oracle solve to 1e-8 (%d iterations, '
+              'residual %.2e), timed' % (n, iters, res))
+    line = {'impl': 'reference', 'metric': METRIC, 'value': round(full_ms, 1), 'unit': 'ms',
+            'n_gpus': args.gpus, 'steps': args.steps, 'warmup': args.warmup,
+            'ms_per_step': round(ms_step, 1), 'step': '%d oracle CG iterations' % n,
             'higher_is_better': False, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
             'data': 'synthetic', 'config': config_dict(),
-            'cpu_baseline': dict(cb, value=v),
-            'e2e': {'value': v, 'unit': 'ms', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+            'cpu_baseline': {'value': round(full_ms, 1), 'unit': 'ms', 'cores': cores,
+                             'kind': 'oracle', 'sample': sample,
+                             'extrapolated_from_steps_ms': round(ms_step / (n + 1) * iters, 1)},
+            'e2e': {'value': round(full_ms, 1), 'unit': 'ms', 'h2d_bytes_per_step': 0,
+                    'd2h_bytes_per_step': 0}}
     print(json.dumps(line))
     return 0
 
@@ -235,9 +265,18 @@ def serve_bench(ctx, n_req, sq):
     for t in [ctx.serve_submit(g, pools[k][0], 0.02, 1e-6) for k, g in enumerate(gids)]:
         ctx.serve_poll(t, timeout_us=-1, want_x=False)
     ctx.serve_stats(reset=True)
+    # closed loop: as many clients as slots (4 fields x 8), each submitting
+    # its next request when its previous one has returned
+    from collections import deque
+    clients = 4 * 8
     t0 = time.time()
-    tickets = [submit(i) for i in range(n_req)]
-    bad = sum(ctx.serve_poll(t, timeout_us=-1, want_x=False)[0] != 0 for t in tickets)
+    inflight = deque(submit(i) for i in range(min(clients, n_req)))
+    nxt, bad = len(inflight), 0
+    while inflight:
+        bad += ctx.serve_poll(inflight.popleft(), timeout_us=-1, want_x=False)[0] != 0
+        if nxt < n_req:
+            inflight.append(submit(nxt))
+            nxt += 1
     closed_s = time.time() - t0
     closed = ctx.serve_stats(reset=True)
     rate = 0.8 * n_req / closed_s
@@ -263,15 +302,30 @@ def serve_bench(ctx, n_req, sq):
     open_s = time.time() - t0
     st = ctx.serve_stats()
     bad += sum(x != 0 for x in done)
+    # FP64 error of served solutions: the first two requests of each field,
+    # served again and compared with the plain FP64 GPU CG of the same system
+    sample = []
+    for f in range(4):
+        for i in [k for k in range(n_req) if reqs[k][0] == f][:2]:
+            _, m, t = reqs[i]
+            src = pools[f][i % 8]
+            vh = src.shape[0]
+            status, x, stx = ctx.serve_poll(submit(i), vh=vh, timeout_us=-1)
+            x64, _ = ctx.cg_solve(gids[f], src, m, 1e-10, precision='f64')
+            sample.append({'lattice': 'x'.join(map(str, SERVE_FIELDS[f][0])), 'mass': round(m, 5),
+                           'tol': t, 'status': status, 'true_residual': stx['true_residual'],
+                           'fp64_error_vs_fp64_cg': float(np.linalg.norm(x - x64) /
+                                                          np.linalg.norm(x64))})
     for g in gids:
         ctx.gauge_free(g)
     return {'requests': n_req, 'failed': int(bad),
             'workload': 'volumes uniform over 8^4, 16^3x32, 20^3x64, 24^3x48 (4 resident '
                         'fields), am ~ U[0.005,0.05], tol in {1e-6,1e-8}, 8 slots per field, '
                         'FP32 CG + FP64 reliable updates',
-            'closed_loop': {'solves_per_s': round(n_req / closed_s, 2),
+            'closed_loop': {'clients': clients, 'solves_per_s': round(n_req / closed_s, 2),
                             'p50_ms': round(closed['p50_ms'], 2),
                             'p99_ms': round(closed['p99_ms'], 2)},
+            'fp64_error_sample': sample,
             'open_loop': {'arrival_rate_hz': round(rate, 2), 'seconds': round(open_s, 2),
                           'p50_ms': round(st['p50_ms'], 2), 'p99_ms': round(st['p99_ms'], 2),
                           'mean_ms': round(st['mean_ms'], 2),
@@ -409,6 +463,8 @@ def full_lattice_workload(ctx, sq, stream, fat, lng):
     b = torch.from_numpy(g[..., 0] + 1j * g[..., 1]).cuda()
     ctx.cg_solve_full(gid, b, MASS, TOL, stream=stream)
     ms, (x, st) = timed(lambda: ctx.cg_solve_full(gid, b, MASS, TOL, stream=stream), stream, 2)
+    x64 = ctx.cg_solve_full(gid, b, MASS, 1e-10, precision='f64', stream=stream)[0]
+    err_full = fp64_error(x, x64)
     # BiCGstab on M = m + D itself (the BiCG-family comparison solver): FP64,
     # and FP32 with FP64 reliable updates
     ms_b, (_, stb) = timed(lambda: ctx.bicgstab_solve_full(gid, b, MASS, TOL, stream=stream),
@@ -420,7 +476,8 @@ def full_lattice_workload(ctx, sq, stream, fat, lng):
                                   'am 0.01, tol 1e-8: even-site FP32 CG + FP64 reliable updates, '
                                   'odd sites reconstructed',
                       'ms': round(ms, 3), 'iterations': st['iterations'],
-                      'full_true_residual': st['true_residual']},
+                      'full_true_residual': st['true_residual'],
+                      'fp64_error_vs_fp64_cg': err_full},
             'bicgstab': {'workload': '20^3x64 whole lattice (m + D) x = b, same source, am 0.01, '
                                      'tol 1e-8: FP64 BiCGstab on M itself',
                          'ms': round(ms_b, 1), 'iterations': stb['iterations'],
@@ -814,16 +871,38 @@ def main():
                          (('f32', 18), ('f32', 12), ('i16', 12), ('i16', 18), ('f64', 18)),
                          args.dslash_iters)
     peak, peak_kind = measured_peak()
-    dom = dslash['f32_18']
+    peak_note = (peak_kind + ' (MEASURED_PEAKS.json hbm_gbs)' if peak_kind == 'measured'
+                 else 'fallback')
+    # the CG's own kernels at the launch shape the solve uses (CUDA events
+    # around back-to-back launches inside the library, on `stream`)
+    cg_kernels = {}
+    for mode, name in (('cg_oe', 'D_oe p with <p, A p> (mode 3)'),
+                       ('cg_eo', 'D_eo t with the m^2 epilogue and the update (mode 4)')):
+        us = ctx.time_dslash(gid, 'f32', 18, 1, mode, 200, stream)
+        gbs = CG_KERNEL_BYTES[mode] * vh / (us * 1e-6) / 1e9
+        cg_kernels[mode] = {'kernel': name, 'us': round(us, 2),
+                            'algorithmic_bytes_per_site': CG_KERNEL_BYTES[mode],
+                            'GBs': round(gbs, 1), 'frac': round(gbs / peak, 4)}
+    dom = cg_kernels['cg_eo']
     traffic = None
     if NCU_TRAFFIC['fingerprint'] == kernel_fingerprint():
         traffic = NCU_TRAFFIC['bytes_per_launch']
     roofline = {'bound': 'hbm', 'achieved': dom['GBs'], 'peak': peak, 'unit': 'GB/s',
-                'frac': round(dom['GBs'] / peak, 4), 'traffic': traffic,
-                'kernel': 'dslash_kernel<F32,18-real,1 RHS> (D_oe), %d algorithmic B/site x %d '
-                          'sites per launch' % (DSLASH_BYTES[('f32', 18)], vh),
-                'peak_kind': peak_kind + ' (MEASURED_PEAKS.json hbm_gbs, burst)'
-                if peak_kind == 'measured' else 'fallback'}
+                'frac': dom['frac'], 'traffic': traffic,
+                'kernel': 'dslash_kernel<F32,18-real,1 RHS,MODE_UPDATE> (the CG\'s D_eo kernel '
+                          'with the m^2 epilogue and the update, %.0f%% of the solve), %d '
+                          'algorithmic B/site x %d sites per launch'
+                          % (100 * dom['us'] / (dom['us'] + cg_kernels['cg_oe']['us'] + 4.0),
+                             CG_KERNEL_BYTES['cg_eo'], vh),
+                'us_per_launch': dom['us'], 'peak_kind': peak_note}
+    us_it = ms * 1e3 / iters
+    it_bytes = (CG_KERNEL_BYTES['cg_oe'] + CG_KERNEL_BYTES['cg_eo'] + 72) * vh
+    cg_iteration = {'bytes_per_iteration': it_bytes, 'us_per_iteration': round(us_it, 2),
+                    'GBs': round(it_bytes / (us_it * 1e-6) / 1e9, 1),
+                    'frac': round(it_bytes / (us_it * 1e-6) / 1e9 / peak, 4),
+                    'note': 'whole solve time / iterations (init, reliable updates and the '
+                            'final residual included); bytes: D_oe %d + D_eo %d + xpay 72 B '
+                            'per site' % (CG_KERNEL_BYTES['cg_oe'], CG_KERNEL_BYTES['cg_eo'])}
 
     serve = serve_bench(ctx, args.serve_requests, sq) if args.serve_requests > 0 else None
     extra_i16 = extra_batch = extra_full = extra_npr = None
@@ -868,6 +947,8 @@ def main():
             'whole_lattice_20x64': extra_full,
             'npr_20x64': extra_npr,
             'roofline': roofline,
+            'cg_kernels': cg_kernels,
+            'cg_iteration': cg_iteration,
             'e2e': {'value': round(ms_e2e, 3), 'unit': 'ms', 'h2d_bytes_per_step': h2d,
                     'd2h_bytes_per_step': d2h},
             'gpu_launches': launches,

@@ -318,41 +318,76 @@ __device__ __forceinline__ void pair_hops(const DslashArgs &a, const LinkScales 
 }
 
 // ------------------------------------------------ many systems per thread
-// FP32 tiles of NR >= 2 systems.  One hop matrix is held at a time (18
-// floats), the hop's sign (eta, backward hop, antiperiodic wrap) is folded
-// into it once, and it is applied to the gathered neighbour vector of every
-// system of the tile, so the per-system work is the 16 gathers and the
-// 16 x 36 FMAs of the mat-vecs and nothing else.  Holding one matrix
-// instead of a direction's four keeps 12 systems' accumulators in
-// registers.  The matrices of a pair share the middle 16-byte plane of the
-// pair (its first two floats end matrix 0, its last two begin matrix 1).
-template <int RECON, int KIND, int H>
-__device__ __forceinline__ void f32_load_hop(const char *pair, int S, int i, uint64_t pol,
-                                             float (&keep)[2], const LinkScales &ls,
-                                             Mat3<float> &m) {
-  constexpr bool k12 = (KIND == 1 && RECON == 12);
-  constexpr int ne = k12 ? 6 : 9;  // stored elements
+// FP32 tiles of NR >= 2 systems.  The link stream is staged in shared
+// memory: every thread copies its own site's planes of the next two
+// directions there with cp.async (16 bytes per plane, L2 evict-first) while
+// it computes the current direction, and reads only what it copied itself,
+// so no thread waits for another -- only for its own copy groups
+// (cp.async.wait_group).  The registers left free hold NR systems'
+// accumulators.  One hop matrix is read at a time (18 floats), the hop's
+// sign (eta, backward hop, antiperiodic wrap) is folded into it once, and it
+// is applied to the gathered neighbour vector of every system of the tile,
+// so the per-system work is the 16 gathers and the 16 x 36 FMAs of the
+// mat-vecs.  Shared memory: 2 directions x NPL planes x 16 bytes per thread
+// (NPL = 18 for 18-real long links, 15 for 12-real).
+template <int RECON> struct StagedPlanes {
+  static constexpr int n = LinkLayout<PREC_F32, RECON>::mu_bytes / 16;
+};
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, uint64_t pol) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;"
+               :: "r"(s), "l"(gsrc), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
+}
+
+// Copy the planes of direction mu at site i into stage `buf` (this thread's
+// column of it) and commit them as one group.
+template <int RECON>
+__device__ __forceinline__ void stage_links(const char *links, int S, int i, int mu,
+                                            float4 *buf, uint64_t pol) {
+  constexpr int NPL = StagedPlanes<RECON>::n;
+  const char *src = links + ((size_t)mu * NPL * S + i) * 16;
+#pragma unroll
+  for (int p = 0; p < NPL; ++p)
+    cp_async16(buf + p * blockDim.x + threadIdx.x, src + (size_t)p * S * 16, pol);
+  cp_async_commit();
+}
+
+// Hop matrix H (0: F(x), 1: F(x-mu)^dag, 2: L(x), 3: L(x-3mu)^dag) of the
+// staged direction `buf`.  The two matrices of a pair share its middle plane.
+template <int RECON, int H>
+__device__ __forceinline__ void staged_hop(const float4 *buf, const LinkScales &ls,
+                                           Mat3<float> &m) {
+  constexpr bool k12 = (H >= 2 && RECON == 12);
+  constexpr int ne = k12 ? 6 : 9;
+  constexpr int base = (H >= 2) ? 9 : 0;  // first plane of the pair
+  const int T = blockDim.x;
+  const float4 *b = buf + threadIdx.x;
   float f[20];
   if constexpr (k12) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const float4 q = ld_stream_f4(pair + ((size_t)(3 * H + k) * S + i) * 16, pol);
+      const float4 q = b[(base + 3 * (H - 2) + k) * T];
       f[4 * k] = q.x; f[4 * k + 1] = q.y; f[4 * k + 2] = q.z; f[4 * k + 3] = q.w;
     }
-  } else if constexpr (H == 0) {
+  } else if constexpr ((H & 1) == 0) {
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      const float4 q = ld_stream_f4(pair + ((size_t)k * S + i) * 16, pol);
+      const float4 q = b[(base + k) * T];
       f[4 * k] = q.x; f[4 * k + 1] = q.y; f[4 * k + 2] = q.z; f[4 * k + 3] = q.w;
     }
-    keep[0] = f[18];
-    keep[1] = f[19];
   } else {
-    f[0] = keep[0];
-    f[1] = keep[1];
+    {
+      const float4 q = b[(base + 4) * T];
+      f[0] = q.z; f[1] = q.w;
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const float4 q = ld_stream_f4(pair + ((size_t)(5 + k) * S + i) * 16, pol);
+      const float4 q = b[(base + 5 + k) * T];
       f[2 + 4 * k] = q.x; f[3 + 4 * k] = q.y; f[4 + 4 * k] = q.z; f[5 + 4 * k] = q.w;
     }
   }
@@ -361,46 +396,158 @@ __device__ __forceinline__ void f32_load_hop(const char *pair, int S, int i, uin
   if constexpr (k12) reconstruct_row2(m, ls.recon_f);
 }
 
-template <int RECON, int NR>
+// Neighbour colour vectors of NR systems at the two hops of one pair (the
+// hops' sites nb0, nb1), into registers; inactive systems are skipped.
+template <int NR>
+__device__ __forceinline__ void gather_pair(const DslashArgs &a, int S, int r0,
+                                            const bool (&active)[NR], int nb0, int nb1,
+                                            Vec3<float> (&v)[2][NR]) {
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (!active[r]) continue;
+    const char *f = a.in + (size_t)(r0 + r) * a.in_fb;
+    v[0][r] = SpinorIO<PREC_F32>::load(f, S, nb0);
+    v[1][r] = SpinorIO<PREC_F32>::load(f, S, nb1);
+  }
+}
+
+// acc_r += (s0 M0) v[0][r] + (s1 M1) v[1][r] for one staged pair.
+template <int RECON, int KIND, int NR>
+__device__ __forceinline__ void apply_pair(const float4 *buf, const LinkScales &ls, float s0,
+                                           float s1, const bool (&active)[NR],
+                                           const Vec3<float> (&v)[2][NR],
+                                           Vec3<float> (&acc)[NR]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    Mat3<float> m;
+    if (h == 0) staged_hop<RECON, 2 * KIND>(buf, ls, m);
+    else staged_hop<RECON, 2 * KIND + 1>(buf, ls, m);
+    const float sg = h ? s1 : s0;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) { m.e[e].x *= sg; m.e[e].y *= sg; }
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (active[r]) mat_vec_acc(acc[r], m, v[h][r]);
+  }
+}
+
+// Own-site vectors of the epilogue, staged in the stage buffer that
+// direction 2 has freed while direction 3 is computed, so their load latency
+// hides behind it.  Vector v (in the order p, xs, r of the tile's systems;
+// NORM stages the input at the own index as p) keeps its 16-byte part in
+// slot v and its 8-byte part in half (v & 1) of slot V + v / 2; as many as
+// fit the stage (NPL slots per thread) are staged, the rest are loaded
+// directly in the epilogue.
+template <int MODE, int NR> struct EpiVecs {
+  static constexpr int nvec = (MODE == MODE_UPDATE) ? 3 : (MODE == MODE_NORM || MODE == MODE_MDAGM) ? 1 : 0;
+  static constexpr int total = nvec * NR;
+};
+template <int MODE, int RECON, int NR> struct EpiStage {
+  static constexpr int cap = 2 * StagedPlanes<RECON>::n / 3;
+  static constexpr int V = EpiVecs<MODE, NR>::total < cap ? EpiVecs<MODE, NR>::total : cap;
+};
+
+__device__ __forceinline__ void cp_async16_vec(void *smem_dst, const void *gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(s), "l"(gsrc) : "memory");
+}
+
+// Field of epilogue vector v: the base of system r0 + v % NR's colour vector.
+template <int MODE, int NR>
+__device__ __forceinline__ const char *epi_field(const DslashArgs &a, int r0, int v) {
+  const int k = v / NR, r = r0 + v % NR;
+  if constexpr (MODE == MODE_NORM) return a.in + (size_t)r * a.in_fb;
+  if (k == 0) return a.p + (size_t)r * a.p_fb;
+  if (k == 1) return a.xs + (size_t)r * a.xs_fb;
+  return a.out + (size_t)r * a.out_fb;
+}
+
+template <int MODE, int RECON, int NR>
+__device__ __forceinline__ void stage_epilogue(const DslashArgs &a, int S, int i, int r0,
+                                               const bool (&active)[NR], float4 *buf) {
+  constexpr int V = EpiStage<MODE, RECON, NR>::V;
+  if constexpr (V > 0) {
+    const int T = blockDim.x, t = threadIdx.x;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      if (!active[v % NR]) continue;
+      const char *f = epi_field<MODE, NR>(a, r0, v);
+      cp_async16_vec(buf + v * T + t, f + (size_t)i * 16);
+      cp_async8(reinterpret_cast<char *>(buf + (V + v / 2) * T + t) + 8 * (v & 1),
+                f + (size_t)16 * S + (size_t)i * 8);
+    }
+    cp_async_commit();
+  }
+}
+
+// Epilogue vector v of this thread: from the stage if it was staged, else
+// loaded from its field.
+template <int MODE, int RECON, int NR>
+__device__ __forceinline__ Vec3<float> epi_vec(const DslashArgs &a, int S, int i, int r0, int v,
+                                               const float4 *buf) {
+  constexpr int V = EpiStage<MODE, RECON, NR>::V;
+  if (v < V) {
+    const int T = blockDim.x, t = threadIdx.x;
+    const float4 q = buf[v * T + t];
+    const float2 w = reinterpret_cast<const float2 *>(buf + (V + v / 2) * T + t)[v & 1];
+    Vec3<float> o;
+    o.c[0] = make_float2(q.x, q.y);
+    o.c[1] = make_float2(q.z, q.w);
+    o.c[2] = w;
+    return o;
+  }
+  return SpinorIO<PREC_F32>::load(epi_field<MODE, NR>(a, r0, v), S, i);
+}
+
+// The caller staged directions 0 and 1 (two commit groups) before waiting
+// for its predecessor kernel.  One pair's gathers (2 hops x NR systems) are
+// in flight while the previous pair is multiplied: the loop is bound by the
+// latency of the L2 gathers, and this keeps about twice as many in flight
+// per thread as gathering hop by hop.  (Tiles of 6, 8 and 12 systems, which
+// gathered hop by hop for want of registers, measured 1.7x slower than 4 at
+// 24^3 x 64 with 12 systems.)
+template <int RECON, int NR, int MODE>
 __device__ __forceinline__ void multi_hops(const DslashArgs &a, const LinkScales &ls,
                                            const SiteCoords &sc, int i, int r0,
-                                           const bool (&active)[NR], Vec3<float> (&acc)[NR]) {
-  using LL = LinkLayout<PREC_F32, RECON>;
+                                           const bool (&active)[NR], Vec3<float> (&acc)[NR],
+                                           float4 *stage) {
+  constexpr int NPL = StagedPlanes<RECON>::n;
   const Geom &g = a.g;
   const int S = g.stride;
   const uint64_t pol = l2_link_policy(ls.keep);
+  static_assert(NR <= 4, "FP32 tiles hold 1, 2 or 4 systems");
+  {
+    Vec3<float> vf[2][NR], vl[2][NR];  // fat pair, long pair
+    {
+      float d0, d1;
+      gather_pair<NR>(a, S, r0, active, hop<+1>(g, sc, 0, d0), hop<-1>(g, sc, 0, d1), vf);
+    }
 #pragma unroll 1
-  for (int mu = 0; mu < 4; ++mu) {
-    int nb[4];
-    float f[4];
-    nb[0] = hop<+1>(g, sc, mu, f[0]);
-    nb[1] = hop<-1>(g, sc, mu, f[1]);
-    nb[2] = hop<+3>(g, sc, mu, f[2]);
-    nb[3] = hop<-3>(g, sc, mu, f[3]);
-    const float eta = eta_sign(sc, mu);
-    f[0] *= eta;
-    f[1] *= -eta;
-    f[2] *= eta;
-    f[3] *= -eta;
-    const char *fat = a.links + (size_t)mu * LL::mu_bytes * S;
-    const char *lng = fat + (size_t)LL::fat_bytes * S;
-    float keep[2];
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      Mat3<float> m;
-      if (h == 0) f32_load_hop<RECON, 0, 0>(fat, S, i, pol, keep, ls, m);
-      else if (h == 1) f32_load_hop<RECON, 0, 1>(fat, S, i, pol, keep, ls, m);
-      else if (h == 2) f32_load_hop<RECON, 1, 0>(lng, S, i, pol, keep, ls, m);
-      else f32_load_hop<RECON, 1, 1>(lng, S, i, pol, keep, ls, m);
-#pragma unroll
-      for (int e = 0; e < 9; ++e) { m.e[e].x *= f[h]; m.e[e].y *= f[h]; }
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if (!active[r]) continue;
-        const Vec3<float> v =
-            SpinorIO<PREC_F32>::load(a.in + (size_t)(r0 + r) * a.in_fb, S, nb[h]);
-        mat_vec_acc(acc[r], m, v);
+    for (int mu = 0; mu < 4; ++mu) {
+      float f[4];
+      const int n2 = hop<+3>(g, sc, mu, f[2]);
+      const int n3 = hop<-3>(g, sc, mu, f[3]);
+      hop<+1>(g, sc, mu, f[0]);
+      hop<-1>(g, sc, mu, f[1]);
+      const float eta = eta_sign(sc, mu);
+      gather_pair<NR>(a, S, r0, active, n2, n3, vl);
+      if (mu < 3) cp_async_wait<1>();
+      else cp_async_wait<0>();
+      float4 *buf = stage + (mu & 1) * NPL * blockDim.x;
+      if (mu == 3) stage_epilogue<MODE, RECON, NR>(a, S, i, r0, active, stage);
+      apply_pair<RECON, 0, NR>(buf, ls, eta * f[0], -eta * f[1], active, vf, acc);
+      if (mu < 3) {
+        float d0, d1;
+        gather_pair<NR>(a, S, r0, active, hop<+1>(g, sc, mu + 1, d0),
+                        hop<-1>(g, sc, mu + 1, d1), vf);
       }
+      apply_pair<RECON, 1, NR>(buf, ls, eta * f[2], -eta * f[3], active, vl, acc);
+      // this thread has read direction mu: its stage takes direction mu + 2
+      if (mu + 2 < 4) stage_links<RECON>(a.links, S, i, mu + 2, buf, pol);
     }
   }
 }
@@ -431,6 +578,12 @@ template <int PREC, int NR> struct DslashBounds {
   static constexpr int threads = (PREC == PREC_F64) ? 256 : 512;
   static constexpr int min_blocks = 1;
 };
+// FP32 tiles of several systems: shared memory (the staged links, 576 bytes
+// per thread) bounds them to 384 threads per SM, so up to 168 registers
+template <int NR> struct DslashBounds<PREC_F32, NR> {
+  static constexpr int threads = (NR == 1) ? 512 : 128;
+  static constexpr int min_blocks = (NR == 1) ? 1 : 3;
+};
 // One-RHS 16-bit: six 128-thread blocks per SM (at most 85 registers): the
 // kernel is latency-bound and gains more from resident warps than from
 // registers.
@@ -446,7 +599,16 @@ template <> struct DslashBounds<PREC_F64, 1> {
 inline int dslash_max_block(int prec, int nr) {
   if (prec == PREC_I16 && nr == 1) return DslashBounds<PREC_I16, 1>::threads;
   if (prec == PREC_F64 && nr == 1) return DslashBounds<PREC_F64, 1>::threads;
-  return prec == PREC_F64 ? DslashBounds<PREC_F64, 2>::threads : DslashBounds<PREC_F32, 2>::threads;
+  if (prec == PREC_F32) return nr == 1 ? DslashBounds<PREC_F32, 1>::threads
+                                       : DslashBounds<PREC_F32, 2>::threads;
+  return prec == PREC_F64 ? DslashBounds<PREC_F64, 2>::threads : DslashBounds<PREC_I16, 2>::threads;
+}
+// Dynamic shared memory of a launch: the staged links of the FP32 tiles of
+// several systems (2 directions x planes x 16 bytes per thread).
+inline size_t dslash_smem_bytes(int prec, int recon, int nr, int block) {
+  if (prec != PREC_F32 || nr == 1) return 0;
+  const int npl = (recon == 12) ? 15 : 18;
+  return (size_t)2 * npl * 16 * block;
 }
 
 template <int PREC, int RECON, int NR, int MODE, int OUTP>
@@ -475,8 +637,20 @@ dslash_kernel(const DslashArgs a) {
   if constexpr (kFirst) {
     if (i < g.vh) first.load(a, ls, i);
   }
+  // FP32 tiles of several systems stage directions 0 and 1 of their links in
+  // shared memory (see multi_hops)
+  constexpr bool kStaged = (PREC == PREC_F32 && NR >= 2);
+  extern __shared__ float4 dyn_smem[];
+  if constexpr (kStaged) {
+    if (i < g.vh) {
+      const uint64_t pol = l2_link_policy(ls.keep);
+      constexpr int NPL = StagedPlanes<RECON>::n;
+      stage_links<RECON>(a.links, S, i, 0, dyn_smem, pol);
+      stage_links<RECON>(a.links, S, i, 1, dyn_smem + NPL * blockDim.x, pol);
+    }
+  }
 
-  constexpr bool kPreP = (MODE == MODE_MDAGM || MODE == MODE_UPDATE) && NR < 8;
+  constexpr bool kPreP = (MODE == MODE_MDAGM || MODE == MODE_UPDATE) && NR < 8 && !kStaged;
   Vec3<R> pre[kPreP ? NR : 1];
   if constexpr (kPreP) {
 #pragma unroll
@@ -520,7 +694,10 @@ dslash_kernel(const DslashArgs a) {
       active[r] = (r0 + r < a.nrhs) && slot_active(a.slots + r0 + r, a.gate);
       any_here |= active[r];
     }
-    if (!any_here) return;
+    if (!any_here) {
+      if constexpr (kStaged) cp_async_wait<0>();  // no copy outlives its thread
+      return;
+    }
   } else {
 #pragma unroll
     for (int r = 0; r < NR; ++r) active[r] = (r0 + r < a.nrhs);
@@ -536,8 +713,9 @@ dslash_kernel(const DslashArgs a) {
     const SiteCoords sc = site_coords(g, a.out_parity, i);
     if constexpr (PREC == PREC_I16) {
       i16_hops<RECON, NR>(a, ls, sc, i, r0, active, acc, first.buf);
-    } else if constexpr (PREC == PREC_F32 && NR >= 2) {
-      multi_hops<RECON, NR>(a, ls, sc, i, r0, active, acc);
+    } else if constexpr (kStaged) {
+      multi_hops<RECON, NR, MODE>(a, ls, sc, i, r0, active, acc, dyn_smem);
+      if constexpr (EpiStage<MODE, RECON, NR>::V > 0) cp_async_wait<0>();
     } else if constexpr (PREC == PREC_F64 && NR == 1) {
       pair_hops<PREC, RECON, NR, MODE>(a, ls, sc, i, r0, active, acc);
     } else {
@@ -593,14 +771,15 @@ dslash_kernel(const DslashArgs a) {
     }
   } else if constexpr (MODE == MODE_MDAGM) {
     // Ap = m^2 p - 1/2 acc ; partial Re<p, Ap>
-    double dot[NR];
+    R dot[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      dot[r] = 0.0;
+      dot[r] = 0;
       if (valid && active[r]) {
         const R m2 = (R)(a.slots ? a.slots[r0 + r].m2 : a.m2_const);
         Vec3<R> p;
         if constexpr (kPreP) p = pre[r];
+        else if constexpr (kStaged) p = epi_vec<MODE, RECON, NR>(a, S, i, r0, r, dyn_smem);
         else p = SpinorIO<PREC>::load(a.p + (size_t)(r0 + r) * a.p_fb, S, i);
         Vec3<R> o;
         R d = 0;
@@ -612,7 +791,7 @@ dslash_kernel(const DslashArgs a) {
           d = fma(p.c[c].y, o.c[c].y, d);
         }
         SpinorIO<PREC>::store(a.out + (size_t)(r0 + r) * a.out_fb, S, i, o);
-        dot[r] = (double)d;
+        dot[r] = d;
       }
     }
     if (a.slots != nullptr && a.partial != nullptr && any_here) {
@@ -637,23 +816,25 @@ dslash_kernel(const DslashArgs a) {
   } else if constexpr (MODE == MODE_NORM) {
     // t = D p ; partial |t|^2 + m^2 |p|^2 (p at the own index of the input
     // parity: every input site is counted once)
-    double val[NR];
+    R val[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      val[r] = 0.0;
+      val[r] = 0;
       if (valid && active[r]) {
         Vec3<R> o;
 #pragma unroll
         for (int c = 0; c < 3; ++c) { o.c[c].x = R(0.5) * acc[r].c[c].x; o.c[c].y = R(0.5) * acc[r].c[c].y; }
         SpinorIO<PREC>::store(a.out + (size_t)(r0 + r) * a.out_fb, S, i, o);
-        const Vec3<R> p = SpinorIO<PREC>::load(a.in + (size_t)(r0 + r) * a.in_fb, S, i);
+        Vec3<R> p;
+        if constexpr (kStaged) p = epi_vec<MODE, RECON, NR>(a, S, i, r0, r, dyn_smem);
+        else p = SpinorIO<PREC>::load(a.in + (size_t)(r0 + r) * a.in_fb, S, i);
         R no = 0, np = 0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           no = fma(o.c[c].x, o.c[c].x, fma(o.c[c].y, o.c[c].y, no));
           np = fma(p.c[c].x, p.c[c].x, fma(p.c[c].y, p.c[c].y, np));
         }
-        val[r] = (double)no + a.slots[r0 + r].m2 * (double)np;
+        val[r] = fma((R)a.slots[r0 + r].m2, np, no);
       }
     }
     if (a.slots != nullptr && a.partial != nullptr && any_here) {
@@ -672,20 +853,24 @@ dslash_kernel(const DslashArgs a) {
     }
   } else if constexpr (MODE == MODE_UPDATE) {
     // Ap = m^2 p - 1/2 acc ; xs += alpha p ; r -= alpha Ap ; partial |r|^2
-    double val[NR];
+    R val[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      val[r] = 0.0;
+      val[r] = 0;
       if (valid && active[r]) {
         const SlotState *sl = a.slots + r0 + r;
         const R m2 = (R)sl->m2, al = (R)sl->alpha;
         Vec3<R> p, rv;
         Vec3<RX> xv;
         if constexpr (kPreP) p = pre[r];
+        else if constexpr (kStaged) p = epi_vec<MODE, RECON, NR>(a, S, i, r0, r, dyn_smem);
         else p = SpinorIO<PREC>::load(a.p + (size_t)(r0 + r) * a.p_fb, S, i);
         if constexpr (kPreRX) {
           rv = pre_r[r];
           xv = pre_x[r];
+        } else if constexpr (kStaged) {
+          xv = epi_vec<MODE, RECON, NR>(a, S, i, r0, NR + r, dyn_smem);
+          rv = epi_vec<MODE, RECON, NR>(a, S, i, r0, 2 * NR + r, dyn_smem);
         } else {
           rv = SpinorIO<PREC>::load(a.out + (size_t)(r0 + r) * a.out_fb, S, i);
           xv = SpinorIO<XP>::load(a.xs + (size_t)(r0 + r) * a.xs_fb, S, i);
@@ -703,7 +888,7 @@ dslash_kernel(const DslashArgs a) {
         }
         SpinorIO<XP>::store(a.xs + (size_t)(r0 + r) * a.xs_fb, S, i, xv);
         SpinorIO<PREC>::store(a.out + (size_t)(r0 + r) * a.out_fb, S, i, rv);
-        val[r] = (double)n2;
+        val[r] = n2;
       }
     }
     if (a.slots != nullptr && a.partial != nullptr && any_here) {
@@ -720,6 +905,7 @@ dslash_kernel(const DslashArgs a) {
           if (active[r]) finish_update(a.slots + r0 + r, rr[r], a.checkpoint);
       }
     }
+
   } else {  // MODE_RESID (PREC == F64)
     double val[3][NR];
 #pragma unroll

@@ -535,6 +535,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 // Reduce NV values per thread over each chunk of the block; thread 0 of every
 // chunk writes partial[v * chunk_stride + chunk] for v < nvalid,
@@ -601,7 +606,11 @@ __device__ __forceinline__ bool last_block_arrived(unsigned *counter, unsigned t
 //   tickets  ngroups + 1 counters of this row (zero on entry; left zero)
 // Returns true in every lane of the single warp that completed the sums;
 // out[v] then holds sum v (all lanes).  All 32 lanes of each warp must call
-// it together.
+// it together.  The values T are double, or float for the sloppy kernels:
+// a warp's 32 sites are then summed in FP32 (GB300 issues FP64 at a small
+// fraction of the FP32 rate, and a multi-system epilogue would otherwise
+// spend more on its FP64 shuffle trees than on its loads), and every sum
+// above the warp -- the accumulation over the lattice -- is in FP64.
 __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
   unsigned old;
   asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
@@ -609,8 +618,8 @@ __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
   return old;
 }
 
-template <int NV>
-__device__ __forceinline__ bool warp_tree_reduce(const double (&val)[NV], int nvalid,
+template <int NV, typename T>
+__device__ __forceinline__ bool warp_tree_reduce(const T (&val)[NV], int nvalid,
                                                  double *const (&inst)[NV], const Geom &g,
                                                  int site, unsigned *tickets,
                                                  double (&out)[NV]) {
@@ -619,8 +628,8 @@ __device__ __forceinline__ bool warp_tree_reduce(const double (&val)[NV], int nv
   if (wc >= g.nwchunks) return false;  // a warp wholly past the last site
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const double sv = warp_sum(val[v]);
-    if (lane == 0 && v < nvalid) inst[v][wc] = sv;
+    const T sv = warp_sum(val[v]);
+    if (lane == 0 && v < nvalid) inst[v][wc] = (double)sv;
   }
   const int grp = wc >> 5;
   const int in_grp = min(32, g.nwchunks - grp * 32);

@@ -177,10 +177,9 @@ DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon
     return def;
   KernelBench kb;
   if (!kb.setup(gf, prec, recon, nrhs, mode, st)) return def;
-  // RHS tiles; the many-RHS tiles (6, 8, 12) exist for the FP32 kernels only
-  // (launch_dslash refuses the others and the candidate is skipped)
+  // RHS tiles (1, 2 or 4 systems per thread)
   std::vector<int> nrs = {1};
-  for (int nr : {2, 4, 6, 8, 12})
+  for (int nr : {2, 4})
     if (nrhs >= nr) nrs.push_back(nr);
   float best = 1e30f;
   DslashConfig best_c = def;
