@@ -43,9 +43,12 @@ DSLASH_FLOPS = 1146
 CG_KERNEL_BYTES = {'cg_oe': 1200, 'cg_eo': 1296}
 CG_FLOPS_PER_SITE_ITER = 2364
 PAPER_CONTEXT_GFLOPS = 46.48   # mixed-precision CG, GTX Titan Black (Table 2)
-# DRAM traffic of one FP32 18-real Dslash launch at 20^3 x 64 from an ncu
-# capture of the kernel source with this fingerprint (None: not captured).
-NCU_TRAFFIC = {'fingerprint': 'd23750f6261c2510', 'bytes_per_launch': 306.2e6}
+# DRAM traffic (read + write) of one launch of the CG's D_eo kernel with the
+# update (FP32, 18-real, 1 RHS, mode 4) at 20^3 x 64 from an ncu capture of
+# the kernel sources with this fingerprint (dram__bytes.sum.per_second x
+# gpu__time_duration.sum; profiles/cg_kernels_20x64.md).  A changed source
+# reports traffic null until it is captured again.
+NCU_TRAFFIC = {'fingerprint': '5b499c8d7ccbb1f0', 'bytes_per_launch': 324.7e6}
 
 
 def parse_args():
@@ -74,6 +77,8 @@ def parse_args():
                    help='profiling aid: only time the two GPU link fattenings (--dims)')
     p.add_argument('--batched-only', action='store_true',
                    help='profiling aid: only run the 24^3x64 multi-RHS / multi-shift workload')
+    p.add_argument('--batched-dslash-only', action='store_true',
+                   help='profiling aid: only time the 12-system Dslash kernels at 24^3x64')
     return p.parse_args()
 
 
@@ -239,8 +244,8 @@ SERVE_FIELDS = [((8, 8, 8, 8), 1), ((16, 16, 16, 32), 2), ((20, 20, 20, 64), 3),
 
 
 def serve_bench(ctx, n_req, sq):
-    """Closed-loop throughput, then Poisson arrivals at 0.8x that rate."""
-    import threading
+    """Closed-loop throughput (32 clients), then Poisson arrivals at 0.8x and
+    0.5x that rate, and the FP64 error of a sample of served solutions."""
     import numpy as np
     import synth
     flags = sq.GAUGE_NO_I16 | sq.GAUGE_NO_LONG12
@@ -279,29 +284,33 @@ def serve_bench(ctx, n_req, sq):
             nxt += 1
     closed_s = time.time() - t0
     closed = ctx.serve_stats(reset=True)
-    rate = 0.8 * n_req / closed_s
-    gaps = rng.exponential(1.0 / rate, n_req)
-    done = []
 
-    def poller(tks):
+    def open_loop(load, n):
+        """Poisson arrivals at `load` x the closed-loop rate, n requests."""
+        rate = load * n_req / closed_s
+        gaps = rng.exponential(1.0 / rate, n)
+        done = []
+        tks = []
+        t0 = time.time()
+        due = t0
+        for i in range(n):
+            due += gaps[i]
+            dt = due - time.time()
+            if dt > 0:
+                time.sleep(dt)
+            tks.append(submit(i))
         for t in tks:
             done.append(ctx.serve_poll(t, timeout_us=-1, want_x=False)[0])
-    tks = []
-    th = None
-    t0 = time.time()
-    due = t0
-    for i in range(n_req):
-        due += gaps[i]
-        dt = due - time.time()
-        if dt > 0:
-            time.sleep(dt)
-        tks.append(submit(i))
-    th = threading.Thread(target=poller, args=(tks,))
-    th.start()
-    th.join()
-    open_s = time.time() - t0
-    st = ctx.serve_stats()
-    bad += sum(x != 0 for x in done)
+        secs = time.time() - t0
+        st = ctx.serve_stats(reset=True)
+        return ({'load': load, 'arrival_rate_hz': round(rate, 2), 'requests': n,
+                 'seconds': round(secs, 2), 'p50_ms': round(st['p50_ms'], 2),
+                 'p99_ms': round(st['p99_ms'], 2), 'mean_ms': round(st['mean_ms'], 2),
+                 'solves_per_s': round(st['solves_per_s'], 2)},
+                sum(x != 0 for x in done))
+    opened, b1 = open_loop(0.8, n_req)
+    half, b2 = open_loop(0.5, n_req // 2)
+    bad += b1 + b2
     # FP64 error of served solutions: the first two requests of each field,
     # served again and compared with the plain FP64 GPU CG of the same system
     sample = []
@@ -326,10 +335,7 @@ def serve_bench(ctx, n_req, sq):
                             'p50_ms': round(closed['p50_ms'], 2),
                             'p99_ms': round(closed['p99_ms'], 2)},
             'fp64_error_sample': sample,
-            'open_loop': {'arrival_rate_hz': round(rate, 2), 'seconds': round(open_s, 2),
-                          'p50_ms': round(st['p50_ms'], 2), 'p99_ms': round(st['p99_ms'], 2),
-                          'mean_ms': round(st['mean_ms'], 2),
-                          'solves_per_s': round(st['solves_per_s'], 2)}}
+            'open_loop': opened, 'open_loop_half_load': half}
 
 
 # 16-bit workload: 32^3 x 64, eps 0.25, am 0.01, tol 1e-8, 16-bit storage with
@@ -742,6 +748,12 @@ def main():
     if args.dslash_only and args.dims:
         dims = tuple(int(v) for v in args.dims.split(','))
     vh = int(np.prod(dims)) // 2
+    if args.batched_dslash_only:
+        ctx = sq.Context(local)
+        print(json.dumps({'dslash_12rhs': batched_dslash(ctx, sq, BATCH_DIMS,
+                                                         torch.cuda.Stream())}))
+        ctx.close()
+        return 0
     if args.batched_only:
         ctx = sq.Context(local)
         print(json.dumps({'batched_24x64': batched_workload(ctx, sq, torch.cuda.Stream())}))

@@ -168,3 +168,38 @@ def test_admission_under_tight_hbm_budget():
             assert oracle.true_residual(dims, fat, lng, 0.05, b, x) <= 1e-8
         s = ctx.serve_stats()
         assert s['hbm_in_use'] <= s['hbm_budget'] == budget
+
+
+def test_full_size_served_requests_match_oracle():
+    """The serving workload's own fields at full size (16^3 x 32 and
+    20^3 x 64, seeds 2 and 3, eps 0.25): served requests at both
+    tolerances, in one mixed stream with a small field beside them, pass the
+    oracle's FP64 residual check and agree with the library's own reported
+    residual -- the same check as the small lattices, at the volumes the
+    benchmark serves."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip('no CUDA device')
+    from paper_1411_2223_gb300 import sq as sqm
+    fields = [((16, 16, 16, 32), 2), ((20, 20, 20, 64), 3), ((8, 8, 8, 8), 1)]
+    flags = sqm.GAUGE_NO_I16 | sqm.GAUGE_NO_LONG12
+    with sqm.Context(0) as ctx:
+        ctx.serve_configure(slots_per_batch=8, block_iters=8)
+        loaded = []
+        for dims, seed in fields:
+            fat, lng = synth.gauge_field(dims, 0.25, seed)
+            loaded.append((dims, ctx.gauge_load(dims, fat, lng, flags=flags), fat, lng))
+        reqs = []
+        for k in range(9):
+            dims, gid, fat, lng = loaded[k % 3]
+            vh = oracle.volume(dims) // 2
+            b = synth.gaussian_source(vh, 10000 * (k % 3) + k)
+            m = 0.005 + 0.005 * k
+            tol = (1e-6, 1e-8)[k % 2]
+            reqs.append((ctx.serve_submit(gid, b, m, tol), dims, fat, lng, b, m, tol))
+        for t, dims, fat, lng, b, m, tol in reqs:
+            status, x, st = ctx.serve_poll(t, vh=oracle.volume(dims) // 2, timeout_us=-1)
+            assert status == 0 and st['status'] == 0, (dims, st)
+            r = oracle.true_residual(dims, fat, lng, m, b, x)
+            assert r <= tol, (dims, m, tol, r)
+            assert abs(st['true_residual'] - r) <= 1e-3 * tol
