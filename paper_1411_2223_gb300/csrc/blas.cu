@@ -1,4 +1,5 @@
-// CG vector kernels (the start r = b, p = r with |b|^2; p = a r + beta p)
+// CG vector kernels (the start r = b, p = r with |b|^2; p = a r + beta p;
+// the scalar steps after the Dslash kernels' reductions)
 // and the canonical <-> packed colour-vector conversions.  The update
 // xs += alpha p, r -= alpha Ap with |r|^2 runs in the epilogue of the second
 // Dslash (MODE_UPDATE of dslash.cuh).  All are bandwidth-bound streaming
@@ -38,6 +39,29 @@ __global__ void __launch_bounds__(256, S == PREC_F64 ? 4 : 8) cg_xpay_kernel(Vec
     p.c[c].y = py;
   }
   SpinorIO<S>::store(a.p + r * a.fb, St, i, p);
+}
+
+// The CG's scalar step after a sloppy Dslash kernel: one block of
+// WIDE_SUM_THREADS per system adds the kernel's per-warp partial sums in a
+// fixed order (block_sum_wide) and runs finish_alpha (KIND 0: after the
+// D_oe kernel, the sum is <p, A p>) or finish_update (KIND 1: after the D_eo
+// kernel, the sum is |r|^2).  Systems the Dslash kernel skipped (not
+// running) are skipped here too.  Launched with programmatic stream
+// serialization, it lets the next Dslash kernel launch -- and prefetch its
+// links -- while it adds.
+template <int KIND>
+__global__ void __launch_bounds__(WIDE_SUM_THREADS) cg_finish_kernel(VecArgs a) {
+  __shared__ double smem[WIDE_SUM_THREADS / 32];
+  griddep_wait();
+  griddep_launch_dependents();
+  SlotState *s = a.slots + blockIdx.x;
+  if (s->status != SLOT_RUNNING) return;  // the same in every thread of the block
+  const double sum =
+      block_sum_wide(a.partial + (size_t)blockIdx.x * red_stride(a.g), a.g.nwchunks, smem);
+  if (threadIdx.x == 0) {
+    if (KIND == 0) finish_alpha(s, sum);
+    else finish_update(s, sum, a.checkpoint);
+  }
 }
 
 // Start of the systems in SLOT_INIT: r = b (sloppy), p = r, x64 = 0; or with
@@ -145,6 +169,14 @@ int launch_cg_xpay(int prec, const VecArgs &a, cudaStream_t st) {
     default: return -1;
   }
   return 0;
+}
+
+int launch_cg_finish(int kind, const VecArgs &a, cudaStream_t st) {
+  if (a.g.vh <= 0) return 0;
+  const dim3 grid(a.nrhs), block(WIDE_SUM_THREADS);
+  cudaError_t e = (kind == 0) ? launch_pdl(cg_finish_kernel<0>, grid, block, 0, st, a)
+                              : launch_pdl(cg_finish_kernel<1>, grid, block, 0, st, a);
+  return e == cudaSuccess ? 0 : -1;
 }
 
 int launch_cg_init(int prec, const VecArgs &a, int guess, cudaStream_t st) {

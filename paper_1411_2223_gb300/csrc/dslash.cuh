@@ -19,13 +19,15 @@
 //               with x = x64 + xs folded into x64 first; r is written in the
 //               sloppy precision OUTP, + partials of |r|^2 and <r, p_sloppy>;
 //               the last block finishes the update
-//   MODE_NORM   out = D in (the CG's D_oe p), + partials of |out|^2 +
-//               m^2 |in|^2 over the own index: that is <p, A p> = |M p|^2
-//               for A = M^dag M restricted to the even sites, since
-//               D_eo = -D_oe^dag; the last warp sets alpha
+//   MODE_NORM   out = D in (the CG's D_oe p), + per-warp partials of
+//               |out|^2 + m^2 |in|^2 over the own index: that is
+//               <p, A p> = |M p|^2 for A = M^dag M restricted to the even
+//               sites, since D_eo = -D_oe^dag; the finish kernel that
+//               follows adds them and sets alpha
 //   MODE_UPDATE Ap = m^2 p - D in, not stored: xs += alpha p, r -= alpha Ap
-//               (r is `out`), + partials of |r|^2; the last warp finishes
-//               the CG step (beta, or a reliable-update request)
+//               (r is `out`), + per-warp partials of |r|^2; the finish
+//               kernel that follows adds them and takes the CG step (beta,
+//               or a reliable-update request)
 // For a reliable update the PLAIN FP64 kernel gathers x64 + xs (the FP64
 // solution plus its sloppy increment since the previous update).
 #pragma once
@@ -67,7 +69,6 @@ struct DslashArgs {
   double *partial;            // [value][rhs][chunk]
   unsigned *counter;
   int gate;
-  int checkpoint;             // UPDATE: a reliable update may be requested now
 };
 
 template <int PREC> struct AccumType { using R = float; };
@@ -842,14 +843,7 @@ dslash_kernel(const DslashArgs a) {
 #pragma unroll
       for (int r = 0; r < NR; ++r)
         inst[r] = a.partial + (size_t)min(r0 + r, a.nrhs - 1) * red_stride(g);
-      double pap[NR];
-      if (warp_tree_reduce<NR>(val, min(NR, a.nrhs - r0), inst, g, i,
-                               a.counter + (size_t)tile * ticket_stride(g), pap) &&
-          (threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int r = 0; r < NR; ++r)
-          if (active[r]) finish_alpha(a.slots + r0 + r, pap[r]);
-      }
+      warp_partials<NR>(val, min(NR, a.nrhs - r0), inst, g, i);
     }
   } else if constexpr (MODE == MODE_UPDATE) {
     // Ap = m^2 p - 1/2 acc ; xs += alpha p ; r -= alpha Ap ; partial |r|^2
@@ -896,14 +890,7 @@ dslash_kernel(const DslashArgs a) {
 #pragma unroll
       for (int r = 0; r < NR; ++r)
         inst[r] = a.partial + (size_t)min(r0 + r, a.nrhs - 1) * red_stride(g);
-      double rr[NR];
-      if (warp_tree_reduce<NR>(val, min(NR, a.nrhs - r0), inst, g, i,
-                               a.counter + (size_t)tile * ticket_stride(g), rr) &&
-          (threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int r = 0; r < NR; ++r)
-          if (active[r]) finish_update(a.slots + r0 + r, rr[r], a.checkpoint);
-      }
+      warp_partials<NR>(val, min(NR, a.nrhs - r0), inst, g, i);
     }
 
   } else {  // MODE_RESID (PREC == F64)

@@ -1,12 +1,13 @@
 // Driver of the batched mixed-precision CG (one system per slot).
 //
-// One iteration is three kernels, gated on device-resident slot state so
-// that no host decision sits inside an iteration:
-//   1. t = D_oe p, <p, A p> = m^2 |p|^2 + |t|^2      (sloppy Dslash; alpha)
+// One iteration is three sloppy kernels and two scalar steps, gated on
+// device-resident slot state so that no host decision sits inside an
+// iteration:
+//   1. t = D_oe p, partials of <p, A p> = m^2 |p|^2 + |t|^2   (sloppy Dslash)
+//      F. sum of the partials: alpha                  (one block per system)
 //   2. Ap = m^2 p - D_eo t (in registers), xs += alpha p, r -= alpha Ap,
-//      |r|^2                                        (sloppy Dslash + epilogue;
-//                                                    beta, or flag a reliable
-//                                                    update)
+//      partials of |r|^2                              (sloppy Dslash + epilogue)
+//      F. sum: beta, or flag a reliable update         (one block per system)
 //   3. p = a r + beta p
 // (<p, A p> = |M p|^2 with M p = (m p, D_oe p), as D_eo = -D_oe^dag.)
 // and after every RU_PERIOD-th iteration (a checkpoint) the reliable-update
@@ -215,6 +216,7 @@ int cg_enqueue_iteration(CGWork *w, cudaStream_t st, int checkpoint) {
   rc = check_launch(w->ctx, launch_dslash(w->prec, w->recon, w->cfg_norm.nr, MODE_NORM,
                                           w->prec, a, w->cfg_norm.block, st));
   if (rc) return rc;
+  if ((rc = check_launch(w->ctx, launch_cg_finish(0, vec_args(w, 0), st)))) return rc;
   // Ap = m^2 p - D_eo t in registers: xs += alpha p, r -= alpha Ap, |r|^2: beta
   DslashArgs b = dslash_args(w, w->prec, w->recon, 0);
   b.in = w->t;
@@ -229,10 +231,14 @@ int cg_enqueue_iteration(CGWork *w, cudaStream_t st, int checkpoint) {
   b.partial = w->partial + w->partial_stride;
   b.counter = w->counters + w->counter_stride;
   b.gate = GATE_RUNNING;
-  b.checkpoint = checkpoint;
   rc = check_launch(w->ctx, launch_dslash(w->prec, w->recon, w->cfg_update.nr, MODE_UPDATE,
                                           w->prec, b, w->cfg_update.block, st));
   if (rc) return rc;
+  {
+    VecArgs f = vec_args(w, 1);
+    f.checkpoint = checkpoint;
+    if ((rc = check_launch(w->ctx, launch_cg_finish(1, f, st)))) return rc;
+  }
   if (checkpoint && (rc = cg_enqueue_ru(w, st))) return rc;
   return cg_enqueue_xpay(w, st);
 }

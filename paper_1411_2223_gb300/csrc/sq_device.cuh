@@ -664,6 +664,55 @@ __device__ __forceinline__ bool warp_tree_reduce(const T (&val)[NV], int nvalid,
   return true;
 }
 
+// First half of warp_tree_reduce alone: every warp stores the shuffle-tree
+// sum of its 32 sites' values as one partial per value (inst[v][site / 32])
+// and goes on; a separate kernel adds the partials (cg_finish_kernel).  No
+// warp waits for a ticket, and the Dslash kernel's last warp has no serial
+// sum to run before the next kernel may start.
+template <int NV, typename T>
+__device__ __forceinline__ void warp_partials(const T (&val)[NV], int nvalid,
+                                              double *const (&inst)[NV], const Geom &g,
+                                              int site) {
+  const int lane = threadIdx.x & 31;
+  const int wc = site >> 5;
+  if (wc >= g.nwchunks) return;  // a warp wholly past the last site
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const T sv = warp_sum(val[v]);
+    if (lane == 0 && v < nvalid) inst[v][wc] = (double)sv;
+  }
+}
+
+// Fixed-order sum of n partials by a block of exactly WIDE_SUM_THREADS
+// threads: thread t adds elements t, t + W, t + 2W, ... in order (eight
+// loads in flight at a time), then a shuffle tree per warp and the warps'
+// sums in order.  The order depends on n only.  All threads of the block
+// call it; the result is valid in thread 0.
+constexpr int WIDE_SUM_THREADS = 1024;
+
+__device__ __forceinline__ double block_sum_wide(const double *p, int n, double *smem) {
+  constexpr int W = WIDE_SUM_THREADS;
+  double s = 0;
+  for (int k0 = threadIdx.x; k0 < n; k0 += 8 * W) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int k = k0 + u * W;
+      v[u] = (k < n) ? __ldcg(p + k) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
+  }
+  s = warp_sum(s);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) smem[warp] = s;
+  __syncthreads();
+  double t = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < W / 32; ++w) t += smem[w];
+  return t;
+}
+
 // Fixed-order sum of n partials: 128 virtual lanes (the block's first 128
 // threads) accumulate strided elements in order k, k + 128, k + 256, ...,
 // then a fixed shuffle tree and the four warp sums in order.  Independent of

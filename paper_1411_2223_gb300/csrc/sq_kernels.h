@@ -21,7 +21,7 @@ struct VecArgs {
   SlotState *slots;
   double *partial;
   unsigned *counter;
-  int checkpoint;     // update kernel: a reliable update may follow this iteration
+  int checkpoint;     // finish after the update: a reliable update may follow this iteration
 };
 
 // Launch with programmatic stream serialization (the kernel must call
@@ -47,6 +47,10 @@ inline int xs_prec(int prec) { return prec == PREC_F64 ? PREC_F64 : PREC_F32; }
 
 int launch_cg_xpay(int prec, const VecArgs &a, cudaStream_t st);
 int launch_cg_init(int prec, const VecArgs &a, int guess, cudaStream_t st);
+// Sum of the per-warp partials the CG's Dslash kernels leave, and the scalar
+// step: kind 0 after the D_oe kernel (alpha), 1 after the D_eo kernel (beta,
+// convergence, reliable-update request; a.checkpoint).
+int launch_cg_finish(int kind, const VecArgs &a, cudaStream_t st);
 
 // canonical complex128 [i][colour] (nrhs fields, canon_elems complex apart)
 int launch_pack(int prec, const Geom &g, const double *canon, size_t canon_elems, void *out,
