@@ -685,8 +685,9 @@ dslash_kernel(const DslashArgs a) {
   griddep_launch_dependents();
 
   // Gate: the decision is the same in every block of a tile row (a system's
-  // state only changes in the warp that completes a reduction over its row,
-  // after every block of the row has read it).  Rows are independent.
+  // state only changes in a later kernel -- a finish kernel -- or in the
+  // warp that completes an in-kernel reduction over its row, after every
+  // block of the row has read it).  Rows are independent.
   bool active[NR];
   bool any_here = false;
   if (a.slots != nullptr && a.gate != GATE_NONE) {
