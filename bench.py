@@ -45,10 +45,10 @@ CG_FLOPS_PER_SITE_ITER = 2364
 PAPER_CONTEXT_GFLOPS = 46.48   # mixed-precision CG, GTX Titan Black (Table 2)
 # DRAM traffic (read + write) of one launch of the CG's D_eo kernel with the
 # update (FP32, 18-real, 1 RHS, mode 4) at 20^3 x 64 from an ncu capture of
-# the kernel sources with this fingerprint (dram__bytes.sum.per_second x
-# gpu__time_duration.sum; profiles/cg_kernels_20x64.md).  A changed source
+# the kernel sources with this fingerprint (dram__bytes_read.sum +
+# dram__bytes_write.sum; profiles/cg_kernels_20x64.md).  A changed source
 # reports traffic null until it is captured again.
-NCU_TRAFFIC = {'fingerprint': '5b499c8d7ccbb1f0', 'bytes_per_launch': 324.7e6}
+NCU_TRAFFIC = {'fingerprint': 'a6bc1f486b479131', 'bytes_per_launch': 324.5e6}
 
 
 def parse_args():

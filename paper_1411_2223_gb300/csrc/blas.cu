@@ -41,26 +41,56 @@ __global__ void __launch_bounds__(256, S == PREC_F64 ? 4 : 8) cg_xpay_kernel(Vec
   SpinorIO<S>::store(a.p + r * a.fb, St, i, p);
 }
 
-// The CG's scalar step after a sloppy Dslash kernel: one block of
-// WIDE_SUM_THREADS per system adds the kernel's per-warp partial sums in a
-// fixed order (block_sum_wide) and runs finish_alpha (KIND 0: after the
-// D_oe kernel, the sum is <p, A p>) or finish_update (KIND 1: after the D_eo
+// The CG's scalar step after a sloppy Dslash kernel: the kernel's per-warp
+// partial sums of each system are added in a fixed order by FINISH_BLOCKS
+// blocks (a fixed partition of the partials, so that the FP64 adds are
+// spread over as many SMs: GB300 issues about two FP64 adds per clock per
+// SM, and one block would spend ~3 us on a 20^3 x 64 lattice's 8000
+// partials alone); the block that arrives last (a ticket per system) adds
+// the block sums in order and runs finish_alpha (KIND 0: after the D_oe
+// kernel, the sum is <p, A p>) or finish_update (KIND 1: after the D_eo
 // kernel, the sum is |r|^2).  Systems the Dslash kernel skipped (not
 // running) are skipped here too.  Launched with programmatic stream
 // serialization, it lets the next Dslash kernel launch -- and prefetch its
 // links -- while it adds.
+constexpr int FINISH_THREADS = 256;
+constexpr int FINISH_BLOCKS = 16;
+
+// Blocks per system for a lattice: at most FINISH_BLOCKS, and no more than
+// the groups of 32 warp partials, whose sum slots hold the block sums.
+inline int finish_blocks(const Geom &g) { return g.ngroups < FINISH_BLOCKS ? g.ngroups : FINISH_BLOCKS; }
+
 template <int KIND>
-__global__ void __launch_bounds__(WIDE_SUM_THREADS) cg_finish_kernel(VecArgs a) {
-  __shared__ double smem[WIDE_SUM_THREADS / 32];
+__global__ void __launch_bounds__(FINISH_THREADS) cg_finish_kernel(VecArgs a) {
+  __shared__ double smem[FINISH_THREADS / 32];
   griddep_wait();
   griddep_launch_dependents();
-  SlotState *s = a.slots + blockIdx.x;
-  if (s->status != SLOT_RUNNING) return;  // the same in every thread of the block
-  const double sum =
-      block_sum_wide(a.partial + (size_t)blockIdx.x * red_stride(a.g), a.g.nwchunks, smem);
+  const int sys = blockIdx.y, j = blockIdx.x, nb = gridDim.x;
+  SlotState *s = a.slots + sys;
+  if (s->status != SLOT_RUNNING) return;  // the same in every block of the system
+  const int n = a.g.nwchunks;
+  double *p = a.partial + (size_t)sys * red_stride(a.g);
+  const int per = (n + nb - 1) / nb;
+  const int k0 = j * per, k1 = min(n, k0 + per);
+  double v = 0.0;
+  for (int k = k0 + (int)threadIdx.x; k < k1; k += FINISH_THREADS) v += __ldcg(p + k);
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) smem[warp] = v;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    if (KIND == 0) finish_alpha(s, sum);
-    else finish_update(s, sum, a.checkpoint);
+    double bs = 0.0;
+#pragma unroll
+    for (int w = 0; w < FINISH_THREADS / 32; ++w) bs += smem[w];
+    p[n + j] = bs;  // the group-sum slots of this reduction instance
+    unsigned *ticket = a.counter + (size_t)sys * ticket_stride(a.g);
+    if (atom_add_acq_rel(ticket, 1u) == (unsigned)(nb - 1)) {
+      double sum = 0.0;
+      for (int b = 0; b < nb; ++b) sum += __ldcg(p + n + b);
+      *ticket = 0;
+      if (KIND == 0) finish_alpha(s, sum);
+      else finish_update(s, sum, a.checkpoint);
+    }
   }
 }
 
@@ -173,7 +203,7 @@ int launch_cg_xpay(int prec, const VecArgs &a, cudaStream_t st) {
 
 int launch_cg_finish(int kind, const VecArgs &a, cudaStream_t st) {
   if (a.g.vh <= 0) return 0;
-  const dim3 grid(a.nrhs), block(WIDE_SUM_THREADS);
+  const dim3 grid(finish_blocks(a.g), a.nrhs), block(FINISH_THREADS);
   cudaError_t e = (kind == 0) ? launch_pdl(cg_finish_kernel<0>, grid, block, 0, st, a)
                               : launch_pdl(cg_finish_kernel<1>, grid, block, 0, st, a);
   return e == cudaSuccess ? 0 : -1;
