@@ -524,7 +524,10 @@ int solve_batch_locked(sq_ctx *ctx, int gauge_id, int nrhs, const double *src,
   const bool dev = (o.flags & SQ_CG_DEVICE_PTRS) != 0;
   const bool guess = (o.flags & SQ_CG_INITIAL_GUESS) != 0;
   const size_t vec_elems = (size_t)3 * gf->g.vh;  // complex per vector
-  if (!dev && !finite_all(src, vec_elems * 2 * nrhs)) return SQ_ERR_NONFINITE;
+  // Non-finite sources are found on the device (|b|^2 of a system is then
+  // not finite and the system ends SLOT_NONFINITE, i.e. SQ_ERR_NONFINITE,
+  // without iterating), as for device pointers: a host pass over the
+  // source would sit between the call and its first copy.
 
   cudaSetDevice(ctx->device);
   auto t0 = std::chrono::steady_clock::now();
