@@ -234,3 +234,40 @@ def test_batched_dslash_every_tile_matches_oracle(tmp_path, monkeypatch, prec, r
                     w = want[par][j]
                     assert rel(got, w) <= TOL_DSLASH[prec], (tile, par, j, rel(got, w))
                     assert site_rel(got, w) <= TOL_DSLASH[prec], (tile, par, j)
+
+
+def test_batched_entry_points_reject_bad_arguments(sq):
+    """dslash_apply_multi, sq_tuned_launch and sq_time_dslash refuse bad
+    batch sizes, modes, precisions and unknown gauge ids with the documented
+    statuses, and sq_time_dslash times the CG's kernels at a positive
+    duration on a real field."""
+    import torch
+    from paper_1411_2223_gb300 import sq as sqm
+    dims = (4, 4, 4, 8)
+    fat, lng = gauge(dims, 0.25, 0)
+    gid = sq.gauge_load(dims, fat, lng, flags=sqm.GAUGE_NO_I16)
+    try:
+        nbytes, _ = sq.spinor_bytes(gid, 'f32')
+        a = torch.zeros(2 * nbytes, dtype=torch.uint8, device='cuda')
+        b = torch.zeros_like(a)
+        cases = [
+            (lambda: sq.dslash_apply_multi(gid, 0, 'f32', 18, 0, a, b), sqm.ERR_ARG),
+            (lambda: sq.dslash_apply_multi(gid, 0, 'f32', 18, 65, a, b), sqm.ERR_ARG),
+            (lambda: sq.dslash_apply_multi(gid, 2, 'f32', 18, 2, a, b), sqm.ERR_ARG),
+            (lambda: sq.dslash_apply_multi(gid, 0, 'f32', 18, 2, a, a), sqm.ERR_ARG),
+            (lambda: sq.dslash_apply_multi(gid + 99, 0, 'f32', 18, 2, a, b), sqm.ERR_NOTFOUND),
+            (lambda: sq.dslash_apply_multi(gid, 0, 'i16', 18, 2, a, b), sqm.ERR_UNSUPPORTED),
+            (lambda: sq.tuned_launch(gid, 'f32', 18, 4, 2), sqm.ERR_ARG),      # mode 2: FP64 only
+            (lambda: sq.tuned_launch(gid, 'f32', 11, 4, 'plain'), sqm.ERR_ARG),
+            (lambda: sq.tuned_launch(gid + 99, 'f32', 18, 4, 'plain'), sqm.ERR_NOTFOUND),
+            (lambda: sq.time_dslash(gid, 'f32', 18, 1, 'cg_oe', reps=0), sqm.ERR_ARG),
+            (lambda: sq.time_dslash(gid, 'f32', 18, 0, 'cg_oe'), sqm.ERR_ARG),
+        ]
+        for k, (call, status) in enumerate(cases):
+            with pytest.raises(sqm.SqError) as e:
+                call()
+            assert e.value.status == status, k
+        for mode in ('plain', 'cg_oe', 'cg_eo'):
+            assert 0.0 < sq.time_dslash(gid, 'f32', 18, 4, mode, reps=3) < 1e5
+    finally:
+        sq.gauge_free(gid)
