@@ -320,17 +320,21 @@ __device__ __forceinline__ void pair_hops(const DslashArgs &a, const LinkScales 
 
 // ------------------------------------------------ many systems per thread
 // FP32 tiles of NR >= 2 systems.  The link stream is staged in shared
-// memory: every thread copies its own site's planes of the next two
-// directions there with cp.async (16 bytes per plane, L2 evict-first) while
-// it computes the current direction, and reads only what it copied itself,
-// so no thread waits for another -- only for its own copy groups
-// (cp.async.wait_group).  The registers left free hold NR systems'
-// accumulators.  One hop matrix is read at a time (18 floats), the hop's
-// sign (eta, backward hop, antiperiodic wrap) is folded into it once, and it
-// is applied to the gathered neighbour vector of every system of the tile,
-// so the per-system work is the 16 gathers and the 16 x 36 FMAs of the
-// mat-vecs.  Shared memory: 2 directions x NPL planes x 16 bytes per thread
-// (NPL = 18 for 18-real long links, 15 for 12-real).
+// memory: every thread copies its own site's planes there with cp.async (16
+// bytes per plane, L2 evict-first) and reads only what it copied itself, so
+// no thread waits for another -- only for its own copy groups
+// (cp.async.wait_group).  The stage holds one direction, as two halves: the
+// fat pair (planes 0-8) and the long pair (planes 9 on); each half of
+// direction mu + 1 is copied while the other half of direction mu is
+// multiplied.  The registers left free hold NR systems' accumulators.  One
+// hop matrix is read at a time (18 floats), the hop's sign (eta, backward
+// hop, antiperiodic wrap) is folded into it once, and it is applied to the
+// gathered neighbour vector of every system of the tile, so the per-system
+// work is the 16 gathers and the 16 x 18 packed FFMA2 of the mat-vecs.
+// Shared memory: NPL planes x 16 bytes per thread (NPL = 18 for 18-real long
+// links, 15 for 12-real).  A stage of two directions measured 10-12 % slower
+// at 24^3 x 64 with 12 systems: its 221 KB per SM left L1 28 KB for the
+// gathered neighbours.
 template <int RECON> struct StagedPlanes {
   static constexpr int n = LinkLayout<PREC_F32, RECON>::mu_bytes / 16;
 };
@@ -345,15 +349,17 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
 }
 
-// Copy the planes of direction mu at site i into stage `buf` (this thread's
-// column of it) and commit them as one group.
-template <int RECON>
-__device__ __forceinline__ void stage_links(const char *links, int S, int i, int mu,
-                                            float4 *buf, uint64_t pol) {
+// Copy half HALF (0: the fat pair's planes 0-8, 1: the long pair's planes 9
+// to NPL - 1) of direction mu at site i into the stage `buf` (this thread's
+// column of it) and commit it as one group.
+template <int RECON, int HALF>
+__device__ __forceinline__ void stage_half(const char *links, int S, int i, int mu, float4 *buf,
+                                           uint64_t pol) {
   constexpr int NPL = StagedPlanes<RECON>::n;
+  constexpr int p0 = HALF ? 9 : 0, p1 = HALF ? NPL : 9;
   const char *src = links + ((size_t)mu * NPL * S + i) * 16;
 #pragma unroll
-  for (int p = 0; p < NPL; ++p)
+  for (int p = p0; p < p1; ++p)
     cp_async16(buf + p * blockDim.x + threadIdx.x, src + (size_t)p * S * 16, pol);
   cp_async_commit();
 }
@@ -412,7 +418,12 @@ __device__ __forceinline__ void gather_pair(const DslashArgs &a, int S, int r0,
   }
 }
 
-// acc_r += (s0 M0) v[0][r] + (s1 M1) v[1][r] for one staged pair.
+// acc_r += (s0 M0) v[0][r] + (s1 M1) v[1][r] for one staged pair, in packed
+// FP32 pairs: with A = s M_ij = (a, b) and A' = (-b, a),
+//   (M v)_i += A (Re v_j, Re v_j) + A' (Im v_j, Im v_j),
+// two FFMA2 per complex multiply-add with one real part of the vector in both
+// lanes, half the FMA instructions of the scalar form.  A and A' are formed
+// once per tile (FMUL2) and serve every system of it.
 template <int RECON, int KIND, int NR>
 __device__ __forceinline__ void apply_pair(const float4 *buf, const LinkScales &ls, float s0,
                                            float s1, const bool (&active)[NR],
@@ -424,27 +435,43 @@ __device__ __forceinline__ void apply_pair(const float4 *buf, const LinkScales &
     if (h == 0) staged_hop<RECON, 2 * KIND>(buf, ls, m);
     else staged_hop<RECON, 2 * KIND + 1>(buf, ls, m);
     const float sg = h ? s1 : s0;
+    // row by row: the two forms of one row (12 registers) are live at a time
 #pragma unroll
-    for (int e = 0; e < 9; ++e) { m.e[e].x *= sg; m.e[e].y *= sg; }
+    for (int i = 0; i < 3; ++i) {
+      float2 A[3], B[3];
 #pragma unroll
-    for (int r = 0; r < NR; ++r)
-      if (active[r]) mat_vec_acc(acc[r], m, v[h][r]);
+      for (int j = 0; j < 3; ++j) {
+        const float2 e = m.e[3 * i + j];
+        A[j] = __fmul2_rn(e, make_float2(sg, sg));
+        B[j] = __fmul2_rn(make_float2(e.y, e.x), make_float2(-sg, sg));
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (!active[r]) continue;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const float2 vj = v[h][r].c[j];
+          acc[r].c[i] = __ffma2_rn(A[j], make_float2(vj.x, vj.x), acc[r].c[i]);
+          acc[r].c[i] = __ffma2_rn(B[j], make_float2(vj.y, vj.y), acc[r].c[i]);
+        }
+      }
+    }
   }
 }
 
-// Own-site vectors of the epilogue, staged in the stage buffer that
-// direction 2 has freed while direction 3 is computed, so their load latency
-// hides behind it.  Vector v (in the order p, xs, r of the tile's systems;
+// Own-site vectors of the epilogue, staged in the fat half of the stage once
+// direction 3's fat pair is multiplied, so their load latency hides behind
+// its long pair.  Vector v (in the order p, xs, r of the tile's systems;
 // NORM stages the input at the own index as p) keeps its 16-byte part in
 // slot v and its 8-byte part in half (v & 1) of slot V + v / 2; as many as
-// fit the stage (NPL slots per thread) are staged, the rest are loaded
-// directly in the epilogue.
+// fit the half (9 slots per thread) are staged, the rest are loaded directly
+// in the epilogue.
 template <int MODE, int NR> struct EpiVecs {
   static constexpr int nvec = (MODE == MODE_UPDATE) ? 3 : (MODE == MODE_NORM || MODE == MODE_MDAGM) ? 1 : 0;
   static constexpr int total = nvec * NR;
 };
 template <int MODE, int RECON, int NR> struct EpiStage {
-  static constexpr int cap = 2 * StagedPlanes<RECON>::n / 3;
+  static constexpr int cap = 2 * 9 / 3;
   static constexpr int V = EpiVecs<MODE, NR>::total < cap ? EpiVecs<MODE, NR>::total : cap;
 };
 
@@ -504,23 +531,23 @@ __device__ __forceinline__ Vec3<float> epi_vec(const DslashArgs &a, int S, int i
   return SpinorIO<PREC_F32>::load(epi_field<MODE, NR>(a, r0, v), S, i);
 }
 
-// The caller staged directions 0 and 1 (two commit groups) before waiting
-// for its predecessor kernel.  One pair's gathers (2 hops x NR systems) are
-// in flight while the previous pair is multiplied: the loop is bound by the
-// latency of the L2 gathers, and this keeps about twice as many in flight
-// per thread as gathering hop by hop.  (Tiles of 6, 8 and 12 systems, which
-// gathered hop by hop for want of registers, measured 1.7x slower than 4 at
-// 24^3 x 64 with 12 systems.)
+// The caller staged both halves of direction 0 (two commit groups) before
+// waiting for its predecessor kernel.  One pair's gathers (2 hops x NR
+// systems) are in flight while the previous pair is multiplied: the loop is
+// bound by the latency of the L2 gathers, and this keeps about twice as many
+// in flight per thread as gathering hop by hop.  (Tiles of 6, 8 and 12
+// systems, which gathered hop by hop for want of registers, measured 1.7x
+// slower than 4 at 24^3 x 64 with 12 systems.)
 template <int RECON, int NR, int MODE>
 __device__ __forceinline__ void multi_hops(const DslashArgs &a, const LinkScales &ls,
                                            const SiteCoords &sc, int i, int r0,
                                            const bool (&active)[NR], Vec3<float> (&acc)[NR],
                                            float4 *stage) {
-  constexpr int NPL = StagedPlanes<RECON>::n;
   const Geom &g = a.g;
   const int S = g.stride;
   const uint64_t pol = l2_link_policy(ls.keep);
   static_assert(NR <= 4, "FP32 tiles hold 1, 2 or 4 systems");
+  constexpr bool kEpi = EpiStage<MODE, RECON, NR>::V > 0;
   {
     Vec3<float> vf[2][NR], vl[2][NR];  // fat pair, long pair
     {
@@ -536,19 +563,23 @@ __device__ __forceinline__ void multi_hops(const DslashArgs &a, const LinkScales
       hop<-1>(g, sc, mu, f[1]);
       const float eta = eta_sign(sc, mu);
       gather_pair<NR>(a, S, r0, active, n2, n3, vl);
-      if (mu < 3) cp_async_wait<1>();
-      else cp_async_wait<0>();
-      float4 *buf = stage + (mu & 1) * NPL * blockDim.x;
-      if (mu == 3) stage_epilogue<MODE, RECON, NR>(a, S, i, r0, active, stage);
-      apply_pair<RECON, 0, NR>(buf, ls, eta * f[0], -eta * f[1], active, vf, acc);
+      // copy groups in flight: [fat mu, long mu]; wait for the fat half
+      cp_async_wait<1>();
+      apply_pair<RECON, 0, NR>(stage, ls, eta * f[0], -eta * f[1], active, vf, acc);
+      // the fat half is read: it takes direction mu + 1's fat pair, or after
+      // direction 3 the epilogue's own-site vectors
+      if (mu < 3) stage_half<RECON, 0>(a.links, S, i, mu + 1, stage, pol);
+      else stage_epilogue<MODE, RECON, NR>(a, S, i, r0, active, stage);
       if (mu < 3) {
         float d0, d1;
         gather_pair<NR>(a, S, r0, active, hop<+1>(g, sc, mu + 1, d0),
                         hop<-1>(g, sc, mu + 1, d1), vf);
       }
-      apply_pair<RECON, 1, NR>(buf, ls, eta * f[2], -eta * f[3], active, vl, acc);
-      // this thread has read direction mu: its stage takes direction mu + 2
-      if (mu + 2 < 4) stage_links<RECON>(a.links, S, i, mu + 2, buf, pol);
+      // in flight: [long mu, next group]; wait for the long half
+      if (mu < 3 || kEpi) cp_async_wait<1>();
+      else cp_async_wait<0>();
+      apply_pair<RECON, 1, NR>(stage, ls, eta * f[2], -eta * f[3], active, vl, acc);
+      if (mu < 3) stage_half<RECON, 1>(a.links, S, i, mu + 1, stage, pol);
     }
   }
 }
@@ -579,8 +610,8 @@ template <int PREC, int NR> struct DslashBounds {
   static constexpr int threads = (PREC == PREC_F64) ? 256 : 512;
   static constexpr int min_blocks = 1;
 };
-// FP32 tiles of several systems: shared memory (the staged links, 576 bytes
-// per thread) bounds them to 384 threads per SM, so up to 168 registers
+// FP32 tiles of several systems: three 128-thread blocks per SM (up to 168
+// registers; the staged links take 288 bytes of shared memory per thread)
 template <int NR> struct DslashBounds<PREC_F32, NR> {
   static constexpr int threads = (NR == 1) ? 512 : 128;
   static constexpr int min_blocks = (NR == 1) ? 1 : 3;
@@ -605,11 +636,11 @@ inline int dslash_max_block(int prec, int nr) {
   return prec == PREC_F64 ? DslashBounds<PREC_F64, 2>::threads : DslashBounds<PREC_I16, 2>::threads;
 }
 // Dynamic shared memory of a launch: the staged links of the FP32 tiles of
-// several systems (2 directions x planes x 16 bytes per thread).
+// several systems (one direction's planes x 16 bytes per thread).
 inline size_t dslash_smem_bytes(int prec, int recon, int nr, int block) {
   if (prec != PREC_F32 || nr == 1) return 0;
   const int npl = (recon == 12) ? 15 : 18;
-  return (size_t)2 * npl * 16 * block;
+  return (size_t)npl * 16 * block;
 }
 
 template <int PREC, int RECON, int NR, int MODE, int OUTP>
@@ -638,16 +669,15 @@ dslash_kernel(const DslashArgs a) {
   if constexpr (kFirst) {
     if (i < g.vh) first.load(a, ls, i);
   }
-  // FP32 tiles of several systems stage directions 0 and 1 of their links in
+  // FP32 tiles of several systems stage direction 0 of their links in
   // shared memory (see multi_hops)
   constexpr bool kStaged = (PREC == PREC_F32 && NR >= 2);
   extern __shared__ float4 dyn_smem[];
   if constexpr (kStaged) {
     if (i < g.vh) {
       const uint64_t pol = l2_link_policy(ls.keep);
-      constexpr int NPL = StagedPlanes<RECON>::n;
-      stage_links<RECON>(a.links, S, i, 0, dyn_smem, pol);
-      stage_links<RECON>(a.links, S, i, 1, dyn_smem + NPL * blockDim.x, pol);
+      stage_half<RECON, 0>(a.links, S, i, 0, dyn_smem, pol);
+      stage_half<RECON, 1>(a.links, S, i, 0, dyn_smem, pol);
     }
   }
 
