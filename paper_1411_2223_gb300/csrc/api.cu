@@ -119,6 +119,7 @@ extern "C" int sq_create(sq_ctx **out, int device, size_t hbm_budget_bytes) {
   SQ_CUDA_TRY(cudaSetDevice(device));
   std::unique_ptr<sq_ctx> c(new sq_ctx());
   c->device = device;
+  SQ_CUDA_TRY(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device));
   SQ_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
   size_t fr = 0, tot = 0;
   SQ_CUDA_TRY(cudaMemGetInfo(&fr, &tot));

@@ -69,6 +69,8 @@ struct DslashArgs {
   double *partial;            // [value][rhs][chunk]
   unsigned *counter;
   int gate;
+  int max_grid;               // > 0: the reliable-update pair's FP64 kernels (PLAIN, RESID)
+                              // run as dslash_gated_kernel on at most this many blocks
 };
 
 template <int PREC> struct AccumType { using R = float; };
@@ -643,18 +645,18 @@ inline size_t dslash_smem_bytes(int prec, int recon, int nr, int block) {
   return (size_t)npl * 16 * block;
 }
 
+// One work item of the kernel: RHS tile blk % ntiles of the blockDim.x
+// sites from (blk / ntiles) * blockDim.x on.  A return ends the item.
 template <int PREC, int RECON, int NR, int MODE, int OUTP>
-__global__ void __launch_bounds__(DslashBounds<PREC, NR>::threads,
-                                  DslashBounds<PREC, NR>::min_blocks)
-dslash_kernel(const DslashArgs a) {
+__device__ __forceinline__ void dslash_item(const DslashArgs &a, const unsigned blk) {
   using R = typename AccumType<PREC>::R;
   const Geom &g = a.g;
   const int S = g.stride;
   // Blocks of the RHS tiles of one range of sites are adjacent in the launch
   // order, so the tiles after the first find that range's links in L2.
   const int ntiles = (a.nrhs + NR - 1) / NR;
-  const int tile = blockIdx.x % ntiles;
-  const int i = (blockIdx.x / ntiles) * blockDim.x + threadIdx.x;
+  const int tile = blk % ntiles;
+  const int i = (blk / ntiles) * blockDim.x + threadIdx.x;
   const int r0 = tile * NR;
   LinkScales ls = a.ls;
   ls.keep = tile < ntiles - 1;  // a later tile of this site range reads the links again
@@ -994,6 +996,65 @@ dslash_kernel(const DslashArgs a) {
       }
     }
   }
+}
+
+// Work items of a launch: site blocks x RHS tiles.
+__host__ __device__ inline int dslash_items(const Geom &g, int nrhs, int nr, int block) {
+  return ((g.vh + block - 1) / block) * ((nrhs + nr - 1) / nr);
+}
+
+// Tiles (of NR systems, at most 64) with a system the gate lets through.
+template <int NR>
+__device__ __forceinline__ unsigned long long active_tiles(const DslashArgs &a, int ntiles) {
+  unsigned long long m = 0;
+  for (int t = 0; t < ntiles; ++t) {
+    bool any = a.slots == nullptr || a.gate == GATE_NONE;
+    for (int r = t * NR; r < min(a.nrhs, (t + 1) * NR) && !any; ++r)
+      any = slot_active(a.slots + r, a.gate);
+    if (any) m |= 1ull << t;
+  }
+  return m;
+}
+
+// Position of the j-th (from 0) set bit of m.
+__device__ __forceinline__ int nth_bit(unsigned long long m, int j) {
+  const unsigned lo = (unsigned)m;
+  const int nlo = __popc(lo);
+  return j < nlo ? (int)__fns(lo, 0, j + 1) : 32 + (int)__fns((unsigned)(m >> 32), 0, j - nlo + 1);
+}
+
+// One block per work item.
+template <int PREC, int RECON, int NR, int MODE, int OUTP>
+__global__ void __launch_bounds__(DslashBounds<PREC, NR>::threads,
+                                  DslashBounds<PREC, NR>::min_blocks)
+dslash_kernel(const DslashArgs a) {
+  dslash_item<PREC, RECON, NR, MODE, OUTP>(a, blockIdx.x);
+}
+
+// Resident blocks per SM of the one-system gated kernels (up to 168
+// registers at 128 threads: the loop around the item must not push the FP64
+// item into spills).
+constexpr int GATED_BLOCKS_PER_SM = 3;
+
+// The FP64 kernels of the reliable-update pair, which have work only at a
+// few of their launches, run on a grid of a few blocks per SM
+// (DslashArgs::max_grid) that share the items of the tiles the gate lets
+// through: item k is site block k / nact of the (k % nact)-th active tile,
+// taken by block k % gridDim.x.  An empty launch costs one wave of blocks,
+// not a block per item, and when some systems need an update every block
+// works on theirs.
+template <int RECON, int NR, int MODE, int OUTP>
+__global__ void __launch_bounds__(DslashBounds<PREC_F64, NR>::threads,
+                                  NR == 1 ? GATED_BLOCKS_PER_SM : DslashBounds<PREC_F64, NR>::min_blocks)
+dslash_gated_kernel(const DslashArgs a) {
+  griddep_wait();  // the gate reads what the previous kernel wrote
+  const int ntiles = (a.nrhs + NR - 1) / NR;
+  const unsigned long long act = active_tiles<NR>(a, ntiles);
+  const int nact = __popcll(act);
+  const int n = nact * ((a.g.vh + (int)blockDim.x - 1) / (int)blockDim.x);
+  for (int k = blockIdx.x; k < n; k += gridDim.x)
+    dslash_item<PREC_F64, RECON, NR, MODE, OUTP>(a, (k / nact) * ntiles + nth_bit(act, k % nact));
+  griddep_launch_dependents();
 }
 
 // Host-side launcher (defined per precision in dslash_*.cu).

@@ -163,9 +163,17 @@ int cg_enqueue_init(CGWork *w, int guess, cudaStream_t st) {
   return SQ_OK;
 }
 
+// The pair has work at few checkpoints: its kernels take a grid of a few
+// blocks per SM that loop over the work items of the systems with a pending
+// update, so that a checkpoint without one costs a wave of blocks (one block
+// per item: 2000 empty blocks per kernel at 20^3 x 64, 41472 for 12 systems
+// at 24^3 x 64).
+static int ru_grid(const CGWork *w) { return GATED_BLOCKS_PER_SM * w->ctx->sms; }
+
 int cg_enqueue_ru(CGWork *w, cudaStream_t st) {
   // t64 = D_oe (x64 + xs) in FP64 for slots with a pending reliable update
   DslashArgs a = dslash_args(w, PREC_F64, 18, 1);
+  a.max_grid = ru_grid(w);
   a.in = w->x64;
   a.in_fb = w->f64_fb;
   a.xs = w->xs;
@@ -194,6 +202,7 @@ int cg_enqueue_ru(CGWork *w, cudaStream_t st) {
   b.partial = w->partial + 2 * w->partial_stride;
   b.counter = w->counters + 2 * w->counter_stride;
   b.gate = GATE_RU;
+  b.max_grid = ru_grid(w);
   return check_launch(w->ctx, launch_dslash(PREC_F64, 18, w->cfg_ru_resid.nr, MODE_RESID,
                                             w->prec, b, w->cfg_ru_resid.block, st));
 }

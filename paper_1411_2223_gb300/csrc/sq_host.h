@@ -60,6 +60,7 @@ struct sq_ctx_impl;
 
 struct sq_ctx {
   int device = 0;
+  int sms = 0;                                       // multiprocessors of the device
   cudaStream_t stream = nullptr;
   size_t budget = 0;
   size_t in_use = 0;
