@@ -149,10 +149,13 @@ def test_many_rhs_tiles_match_oracle(tmp_path, monkeypatch, nr, recon):
     """The FP32 Dslash tiles that apply each link to 2 or 4 systems, forced
     through a tuning cache file (SQ_TUNE_CACHE) onto both kernels of the CG
     iteration (the D_oe kernel with the reduction, mode 3, and the D_eo kernel
-    with the update, mode 4), solve every system of a 12-system batch to the
-    oracle's acceptance, in the iteration counts of the one-system tile (the
-    two tiles add the 16 hop products in different orders, so they agree to
-    rounding, not bit for bit).  The solve reports the tiles it launched."""
+    with the update, mode 4) and onto the FP64 reliable-update pair (its
+    gated kernels, shape key mode 0), solve every system of a 12-system batch
+    with masses 0.02-0.2 (reliable updates for different subsets of the
+    systems) to the oracle's acceptance, in the iteration counts of the
+    one-system tile (the two tiles add the 16 hop products in different
+    orders, so they agree to rounding, not bit for bit).  The solve reports
+    the tiles it launched."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip('no CUDA device')
@@ -169,7 +172,8 @@ def test_many_rhs_tiles_match_oracle(tmp_path, monkeypatch, nr, recon):
     for tile in (1, nr):
         cache = tmp_path / ('tune_%d.txt' % tile)
         cache.write_text(''.join('dslash_v4:%s:p1:r%d:n%d:m%d 128 %d\n' % (lat, recon, nrhs, m, tile)
-                                 for m in (3, 4)))
+                                 for m in (3, 4)) +
+                         'dslash_v4:%s:p0:r18:n%d:m0 128 %d\n' % (lat, nrhs, tile))
         monkeypatch.setenv('SQ_TUNE_CACHE', str(cache))
         with sqm.Context(0) as ctx:
             gid = ctx.gauge_load(dims, fat, lng)
