@@ -466,8 +466,8 @@ __device__ __forceinline__ void apply_pair(const float4 *buf, const LinkScales &
 // its long pair.  Vector v (in the order p, xs, r of the tile's systems;
 // NORM stages the input at the own index as p) keeps its 16-byte part in
 // slot v and its 8-byte part in half (v & 1) of slot V + v / 2; as many as
-// fit the half (9 slots per thread) are staged, the rest are loaded directly
-// in the epilogue.
+// fit the half (9 slots per thread) are staged, the rest go to registers
+// (EpiRest).
 template <int MODE, int NR> struct EpiVecs {
   static constexpr int nvec = (MODE == MODE_UPDATE) ? 3 : (MODE == MODE_NORM || MODE == MODE_MDAGM) ? 1 : 0;
   static constexpr int total = nvec * NR;
@@ -514,23 +514,47 @@ __device__ __forceinline__ void stage_epilogue(const DslashArgs &a, int S, int i
   }
 }
 
-// Epilogue vector v of this thread: from the stage if it was staged, else
-// loaded from its field.
+// The caller staged both halves of direction 0 (two commit groups) before
+// waiting for its predecessor kernel.  One pair's gathers (2 hops x NR
+// systems) are in flight while the previous pair is multiplied: the loop is
+// bound by the latency of the L2 gathers, and this keeps about twice as many
+// in flight per thread as gathering hop by hop.  (Tiles of 6, 8 and 12
+// systems, which gathered hop by hop for want of registers, measured 1.7x
+// slower than 4 at 24^3 x 64 with 12 systems.)
+// The epilogue's own-site vectors that do not fit the stage (mode 4: 6 of
+// its 12) are loaded during direction 3's long pair into the fat-pair gather
+// buffer, which has no next direction to hold: vector V + k in slot
+// [k / NR][k % NR].
+template <int MODE, int RECON, int NR> struct EpiRest {
+  static constexpr int n = EpiVecs<MODE, NR>::total - EpiStage<MODE, RECON, NR>::V;
+  static_assert(n <= 2 * NR, "the rest of the epilogue vectors fits the fat-pair buffer");
+  __device__ __forceinline__ static void load(const DslashArgs &a, int S, int i, int r0,
+                                              const bool (&active)[NR], Vec3<float> (&buf)[2][NR]) {
+    constexpr int V = EpiStage<MODE, RECON, NR>::V;
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+      if (active[(V + k) % NR])
+        buf[k / NR][k % NR] = SpinorIO<PREC_F32>::load(epi_field<MODE, NR>(a, r0, V + k), S, i);
+  }
+};
+
+// Epilogue vector v of this thread: from the stage, or from the fat-pair
+// buffer the last direction loaded it into.
 template <int MODE, int RECON, int NR>
-__device__ __forceinline__ Vec3<float> epi_vec(const DslashArgs &a, int S, int i, int r0, int v,
-                                               const float4 *buf) {
+__device__ __forceinline__ Vec3<float> epi_vec(const float4 *stage, const Vec3<float> (&buf)[2][NR],
+                                               int v) {
   constexpr int V = EpiStage<MODE, RECON, NR>::V;
   if (v < V) {
     const int T = blockDim.x, t = threadIdx.x;
-    const float4 q = buf[v * T + t];
-    const float2 w = reinterpret_cast<const float2 *>(buf + (V + v / 2) * T + t)[v & 1];
+    const float4 q = stage[v * T + t];
+    const float2 w = reinterpret_cast<const float2 *>(stage + (V + v / 2) * T + t)[v & 1];
     Vec3<float> o;
     o.c[0] = make_float2(q.x, q.y);
     o.c[1] = make_float2(q.z, q.w);
     o.c[2] = w;
     return o;
   }
-  return SpinorIO<PREC_F32>::load(epi_field<MODE, NR>(a, r0, v), S, i);
+  return buf[(v - V) / NR][(v - V) % NR];
 }
 
 // The caller staged both halves of direction 0 (two commit groups) before
@@ -539,50 +563,51 @@ __device__ __forceinline__ Vec3<float> epi_vec(const DslashArgs &a, int S, int i
 // bound by the latency of the L2 gathers, and this keeps about twice as many
 // in flight per thread as gathering hop by hop.  (Tiles of 6, 8 and 12
 // systems, which gathered hop by hop for want of registers, measured 1.7x
-// slower than 4 at 24^3 x 64 with 12 systems.)
+// slower than 4 at 24^3 x 64 with 12 systems.)  vf, the fat-pair buffer,
+// holds the epilogue's unstaged own-site vectors on return.
 template <int RECON, int NR, int MODE>
 __device__ __forceinline__ void multi_hops(const DslashArgs &a, const LinkScales &ls,
                                            const SiteCoords &sc, int i, int r0,
                                            const bool (&active)[NR], Vec3<float> (&acc)[NR],
-                                           float4 *stage) {
+                                           float4 *stage, Vec3<float> (&vf)[2][NR]) {
   const Geom &g = a.g;
   const int S = g.stride;
   const uint64_t pol = l2_link_policy(ls.keep);
   static_assert(NR <= 4, "FP32 tiles hold 1, 2 or 4 systems");
   constexpr bool kEpi = EpiStage<MODE, RECON, NR>::V > 0;
+  Vec3<float> vl[2][NR];  // long pair
   {
-    Vec3<float> vf[2][NR], vl[2][NR];  // fat pair, long pair
-    {
-      float d0, d1;
-      gather_pair<NR>(a, S, r0, active, hop<+1>(g, sc, 0, d0), hop<-1>(g, sc, 0, d1), vf);
-    }
+    float d0, d1;
+    gather_pair<NR>(a, S, r0, active, hop<+1>(g, sc, 0, d0), hop<-1>(g, sc, 0, d1), vf);
+  }
 #pragma unroll 1
-    for (int mu = 0; mu < 4; ++mu) {
-      float f[4];
-      const int n2 = hop<+3>(g, sc, mu, f[2]);
-      const int n3 = hop<-3>(g, sc, mu, f[3]);
-      hop<+1>(g, sc, mu, f[0]);
-      hop<-1>(g, sc, mu, f[1]);
-      const float eta = eta_sign(sc, mu);
-      gather_pair<NR>(a, S, r0, active, n2, n3, vl);
-      // copy groups in flight: [fat mu, long mu]; wait for the fat half
-      cp_async_wait<1>();
-      apply_pair<RECON, 0, NR>(stage, ls, eta * f[0], -eta * f[1], active, vf, acc);
-      // the fat half is read: it takes direction mu + 1's fat pair, or after
-      // direction 3 the epilogue's own-site vectors
-      if (mu < 3) stage_half<RECON, 0>(a.links, S, i, mu + 1, stage, pol);
-      else stage_epilogue<MODE, RECON, NR>(a, S, i, r0, active, stage);
-      if (mu < 3) {
-        float d0, d1;
-        gather_pair<NR>(a, S, r0, active, hop<+1>(g, sc, mu + 1, d0),
-                        hop<-1>(g, sc, mu + 1, d1), vf);
-      }
-      // in flight: [long mu, next group]; wait for the long half
-      if (mu < 3 || kEpi) cp_async_wait<1>();
-      else cp_async_wait<0>();
-      apply_pair<RECON, 1, NR>(stage, ls, eta * f[2], -eta * f[3], active, vl, acc);
-      if (mu < 3) stage_half<RECON, 1>(a.links, S, i, mu + 1, stage, pol);
+  for (int mu = 0; mu < 4; ++mu) {
+    float f[4];
+    const int n2 = hop<+3>(g, sc, mu, f[2]);
+    const int n3 = hop<-3>(g, sc, mu, f[3]);
+    hop<+1>(g, sc, mu, f[0]);
+    hop<-1>(g, sc, mu, f[1]);
+    const float eta = eta_sign(sc, mu);
+    gather_pair<NR>(a, S, r0, active, n2, n3, vl);
+    // copy groups in flight: [fat mu, long mu]; wait for the fat half
+    cp_async_wait<1>();
+    apply_pair<RECON, 0, NR>(stage, ls, eta * f[0], -eta * f[1], active, vf, acc);
+    // the fat half is read: it takes direction mu + 1's fat pair, or after
+    // direction 3 the epilogue's own-site vectors
+    if (mu < 3) {
+      stage_half<RECON, 0>(a.links, S, i, mu + 1, stage, pol);
+      float d0, d1;
+      gather_pair<NR>(a, S, r0, active, hop<+1>(g, sc, mu + 1, d0),
+                      hop<-1>(g, sc, mu + 1, d1), vf);
+    } else {
+      stage_epilogue<MODE, RECON, NR>(a, S, i, r0, active, stage);
+      EpiRest<MODE, RECON, NR>::load(a, S, i, r0, active, vf);
     }
+    // in flight: [long mu, next group]; wait for the long half
+    if (mu < 3 || kEpi) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    apply_pair<RECON, 1, NR>(stage, ls, eta * f[2], -eta * f[3], active, vl, acc);
+    if (mu < 3) stage_half<RECON, 1>(a.links, S, i, mu + 1, stage, pol);
   }
 }
 
@@ -742,13 +767,14 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const unsigned 
   Vec3<R> acc[NR];
 #pragma unroll
   for (int r = 0; r < NR; ++r) zero(acc[r]);
+  Vec3<float> vbuf[kStaged ? 2 : 1][kStaged ? NR : 1];  // staged tiles: the fat-pair gathers
 
   if (valid) {
     const SiteCoords sc = site_coords(g, a.out_parity, i);
     if constexpr (PREC == PREC_I16) {
       i16_hops<RECON, NR>(a, ls, sc, i, r0, active, acc, first.buf);
     } else if constexpr (kStaged) {
-      multi_hops<RECON, NR, MODE>(a, ls, sc, i, r0, active, acc, dyn_smem);
+      multi_hops<RECON, NR, MODE>(a, ls, sc, i, r0, active, acc, dyn_smem, vbuf);
       if constexpr (EpiStage<MODE, RECON, NR>::V > 0) cp_async_wait<0>();
     } else if constexpr (PREC == PREC_F64 && NR == 1) {
       pair_hops<PREC, RECON, NR, MODE>(a, ls, sc, i, r0, active, acc);
@@ -813,7 +839,7 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const unsigned 
         const R m2 = (R)(a.slots ? a.slots[r0 + r].m2 : a.m2_const);
         Vec3<R> p;
         if constexpr (kPreP) p = pre[r];
-        else if constexpr (kStaged) p = epi_vec<MODE, RECON, NR>(a, S, i, r0, r, dyn_smem);
+        else if constexpr (kStaged) p = epi_vec<MODE, RECON, NR>(dyn_smem, vbuf, r);
         else p = SpinorIO<PREC>::load(a.p + (size_t)(r0 + r) * a.p_fb, S, i);
         Vec3<R> o;
         R d = 0;
@@ -860,7 +886,7 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const unsigned 
         for (int c = 0; c < 3; ++c) { o.c[c].x = R(0.5) * acc[r].c[c].x; o.c[c].y = R(0.5) * acc[r].c[c].y; }
         SpinorIO<PREC>::store(a.out + (size_t)(r0 + r) * a.out_fb, S, i, o);
         Vec3<R> p;
-        if constexpr (kStaged) p = epi_vec<MODE, RECON, NR>(a, S, i, r0, r, dyn_smem);
+        if constexpr (kStaged) p = epi_vec<MODE, RECON, NR>(dyn_smem, vbuf, r);
         else p = SpinorIO<PREC>::load(a.in + (size_t)(r0 + r) * a.in_fb, S, i);
         R no = 0, np = 0;
 #pragma unroll
@@ -890,14 +916,14 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const unsigned 
         Vec3<R> p, rv;
         Vec3<RX> xv;
         if constexpr (kPreP) p = pre[r];
-        else if constexpr (kStaged) p = epi_vec<MODE, RECON, NR>(a, S, i, r0, r, dyn_smem);
+        else if constexpr (kStaged) p = epi_vec<MODE, RECON, NR>(dyn_smem, vbuf, r);
         else p = SpinorIO<PREC>::load(a.p + (size_t)(r0 + r) * a.p_fb, S, i);
         if constexpr (kPreRX) {
           rv = pre_r[r];
           xv = pre_x[r];
         } else if constexpr (kStaged) {
-          xv = epi_vec<MODE, RECON, NR>(a, S, i, r0, NR + r, dyn_smem);
-          rv = epi_vec<MODE, RECON, NR>(a, S, i, r0, 2 * NR + r, dyn_smem);
+          xv = epi_vec<MODE, RECON, NR>(dyn_smem, vbuf, NR + r);
+          rv = epi_vec<MODE, RECON, NR>(dyn_smem, vbuf, 2 * NR + r);
         } else {
           rv = SpinorIO<PREC>::load(a.out + (size_t)(r0 + r) * a.out_fb, S, i);
           xv = SpinorIO<XP>::load(a.xs + (size_t)(r0 + r) * a.xs_fb, S, i);
