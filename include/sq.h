@@ -375,7 +375,7 @@ int cg_solve_multi(sq_ctx *ctx, int gauge_id, int nrhs, const double *src,
 /* Multi-shift CG (not in the paper; the masses of Sec. 2's inverter solved
  * together): (m_i^2 - D_eo D_oe) x_i = b for nshift masses from one Krylov
  * space (Jegerlehner's shifted recurrences, hep-lat/9612014), run in the sloppy
- * precision to max(tol, 1e-5 for FP32 / 1e-3 for 16-bit), then refined per
+ * precision to max(tol, 1e-6 for FP32 / 1e-3 for 16-bit), then refined per
  * shift by the batched mixed-precision CG above started from the shifted
  * solutions.  x: nshift canonical vectors; stats: nshift entries (may be NULL). */
 int cg_solve_multishift(sq_ctx *ctx, int gauge_id, const double *src, int nshift,
