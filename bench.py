@@ -382,6 +382,7 @@ def i16_workload(ctx, sq, stream, dslash_iters):
     ms16, st16 = timed(lambda: solve('i16', 12), stream, 2)
     x16 = x.clone()
     ms64, st64 = timed(lambda: solve('f64', 18), stream, 1)
+    err_same_tol = fp64_error(x16, x)  # against the FP64 CG to the same tol
     ctx.cg_solve(gid, b, MASS, 1e-10, precision='f64', stream=stream, out=x)
     err = fp64_error(x16, x)
     dsl = time_dslash(ctx, gid, b, stream, vh, (('i16', 12), ('i16', 18)), dslash_iters)
