@@ -10,7 +10,8 @@ int launch_dslash_i16(int, int, int, int, const DslashArgs &, int, cudaStream_t)
 int launch_dslash(int prec, int recon, int nr, int mode, int outp, const DslashArgs &a,
                   int block, cudaStream_t stream) {
   if (a.g.vh <= 0) return 0;
-  if (block <= 0 || block % CHUNK != 0 || block > 512) return -1;
+  // whole warps (the kernels' sums are per warp of 32 sites), at most 512
+  if (block <= 0 || block % 32 != 0 || block > 512) return -1;
   const int cap = dslash_max_block(prec, nr);
   if (block > cap) block = cap;
   switch (prec) {

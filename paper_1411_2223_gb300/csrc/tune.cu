@@ -205,7 +205,9 @@ DslashConfig tuned_dslash(sq_ctx *ctx, const GaugeField &gf, int prec, int recon
   // the previous one as back-to-back launches of one kernel do: there the
   // smallest block within 3 % of the best isolated time wins (20^3 x 64
   // solve, one box: 128/128 threads 43.5 ms, the isolated pick 256/128
-  // 44.0 ms, 512/384 46.1 ms).
+  // 44.0 ms, 512/384 46.1 ms).  64-thread blocks are not candidates: forced,
+  // they gave 42.7 against 43.1 ms on one box, but as the tuner's pick the
+  // 20^3 x 64 solves lost 3 % (FP32) and 10 % (16-bit) on another.
   if (mode != MODE_PLAIN)
     for (const auto &ct : timed)
       if (ct.first.nr == best_c.nr && ct.first.block < best_c.block && ct.second <= 1.03f * best)

@@ -245,7 +245,7 @@ def test_solution_bits_independent_of_block_size(tmp_path, monkeypatch):
     b = synth.gaussian_source(oracle.volume(dims) // 2, 7)
     lat = 'x'.join(map(str, dims))
     xs = []
-    for block in (128, 256, 512):
+    for block in (64, 128, 256, 512):
         cache = tmp_path / ('tune_%d.txt' % block)
         cache.write_text(''.join('dslash_v4:%s:p%d:r18:n1:m%d %d 1\n' % (lat, p, m, block)
                                  for p, m in ((1, 3), (1, 4), (0, 0))))
@@ -257,5 +257,5 @@ def test_solution_bits_independent_of_block_size(tmp_path, monkeypatch):
         assert (st['oe_block'], st['eo_block']) == (block, block), st
         assert (st['oe_rhs_tile'], st['eo_rhs_tile']) == (1, 1), st
         xs.append(x)
-    assert np.array_equal(xs[0], xs[1]) and np.array_equal(xs[0], xs[2])
+    assert all(np.array_equal(xs[0], x) for x in xs[1:])
     assert oracle.true_residual(dims, fat, lng, 0.05, b, xs[0]) <= 1e-9
