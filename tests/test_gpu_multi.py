@@ -275,3 +275,28 @@ def test_batched_entry_points_reject_bad_arguments(sq):
             assert 0.0 < sq.time_dslash(gid, 'f32', 18, 4, mode, reps=3) < 1e5
     finally:
         sq.gauge_free(gid)
+
+
+def test_64_system_batch_matches_oracle(sq):
+    """The largest batch, 64 systems with 64 masses from 0.02 to 0.5 (the
+    systems converge, and need their reliable updates, at different
+    iterations): the reliable-update kernels' active-tile mask then spans
+    both halves of its 64 bits.  Every system meets the oracle's residual."""
+    dims = (4, 4, 4, 6)
+    fat, lng = gauge(dims, 0.25, 0)
+    vh = oracle.volume(dims) // 2
+    nrhs = 64
+    srcs = synth.gaussian_sources(vh, range(100, 100 + nrhs))
+    masses = np.geomspace(0.02, 0.5, nrhs)
+    tol = 1e-8
+    gid = sq.gauge_load(dims, fat, lng)
+    try:
+        xs, stats, status = sq.cg_solve_multi(gid, srcs, masses, tol)
+        assert status == 0
+        its = [s['iterations'] for s in stats]
+        assert its[0] > its[-1]
+        for j in range(nrhs):
+            assert stats[j]['status'] == 0
+            assert oracle.true_residual(dims, fat, lng, masses[j], srcs[j], xs[j]) <= tol
+    finally:
+        sq.gauge_free(gid)
