@@ -302,7 +302,9 @@ int dslash_apply_multi(sq_ctx *ctx, int gauge_id, int out_parity, int prec, int 
  * 1 with the m^2 epilogue (mdagm_apply, multi-shift), 3 the CG's D_oe kernel
  * with its reduction, 4 the CG's D_eo kernel with its update.  The shape is
  * chosen by timing the candidates on first use (which allocates scratch and
- * synchronises `stream`) unless SQ_TUNE_CACHE or an earlier call fixed it.
+ * synchronises `stream`) unless SQ_TUNE_CACHE or an earlier call fixed it;
+ * for modes 1, 3 and 4, which run in chains of dependent launches, the
+ * smallest block within 3 % of the fastest is taken.
  * (The paper's QUDA path tunes its launches at run time, Sec. 3.) */
 int sq_tuned_launch(sq_ctx *ctx, int gauge_id, int prec, int long_recon, int nrhs, int mode,
                     void *stream, int *block, int *rhs_tile);
